@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Tree-build throughput on one GB300 (or N replicas).
+
+A step is one full build of the hashed oct-tree -- root cell, keys, radix
+sort, leaves, cells with links, moments (tb_build + tb_moments) -- over one
+batch of synthetic particles already resident in HBM.  The default workload
+is the 2^27-particle clustered-halo set (n_crit = 16).  Prints one JSON line
+(rank 0):
+
+  value        Mparticles/s over the K timed steps (device events, max over
+               ranks, all ranks' particles)
+  roofline     the dominant kernel (one radix-sort pass): algorithmic bytes
+               per launch / its mean event-timed duration, against the
+               measured HBM copy bandwidth
+  cpu_baseline the FP64 oracle, single thread, on a bounded sample
+  e2e          the same metric through the C ABI from pinned host buffers,
+               host<->device copies inside the timed region
+  batched      (when built) batched vs plain per-set builds, same GB300
+
+--impl reference times the oracle instead (the reference arm of the
+comparison): host cores, bounded sample, same metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS, batched_plummer, workload  # noqa: E402
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
+# the digest of the kernel source it was taken on; reported only while the
+# source is unchanged (see profiles/).
+NCU_TRAFFIC = {}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clustered_2p27", choices=sorted(
+        k for k, v in WORKLOADS.items() if v["kind"] != "batched"))
+    ap.add_argument("--n", type=int, default=0, help="override particle count")
+    ap.add_argument("--n-crit", type=int, default=0)
+    ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 21)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=100)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in ("tb_sort.cu", "tb_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2312_06102_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gen(wl: str, n_override: int):
+    spec = dict(WORKLOADS[wl])
+    n = n_override or spec["n"]
+    t0 = time.perf_counter()
+    pos, mass = workload(spec["kind"], n, spec["seed"])
+    log(f"[bench] generated {wl} n={n} in {time.perf_counter() - t0:.1f}s")
+    return pos, mass, spec, n
+
+
+def oracle_rate(pos, mass, n_crit, sample):
+    """FP64 oracle (single thread): full build + direct-sum moments of the
+    first `sample` particles; returns (Mparticles/s, seconds, particles)."""
+    import oracle
+    m = min(sample, pos.shape[0])
+    p, w = np.ascontiguousarray(pos[:m]), np.ascontiguousarray(mass[:m])
+    t0 = time.perf_counter()
+    t = oracle.build_tree(p, n_crit)
+    oracle.moments(t, p, w)
+    dt = time.perf_counter() - t0
+    return m / dt / 1e6, dt, m
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pos, mass, spec, n = gen(a.workload, a.n)
+    n_crit = a.n_crit or spec["n_crit"]
+    import oracle
+    oracle.build()
+    m = min(a.cpu_sample, n)
+    for _ in range(max(0, min(a.warmup, 1))):
+        oracle_rate(pos, mass, n_crit, min(m, 1 << 16))
+    times = []
+    for _ in range(a.steps):
+        r, dt, _ = oracle_rate(pos, mass, n_crit, m)
+        times.append(dt)
+    tot = sum(times)
+    value = m * len(times) / tot / 1e6
+    sample = f"first {m} of the {n} particles of {a.workload}, full FP64 build + direct-sum moments"
+    out = {"metric": "tree-build Mparticles/s", "value": round(value, 4), "unit": "Mparticles/s",
+           "impl": "reference", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": a.workload, "n_particles": n, "n_crit": n_crit},
+           "cpu_baseline": {"value": round(value, 4), "unit": "Mparticles/s", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "Mparticles/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2312_06102_gb300 as tb
+    tb.lib()
+
+    pos, mass, spec, n = gen(a.workload, a.n)
+    n_crit = a.n_crit or spec["n_crit"]
+    hpos = torch.from_numpy(pos).pin_memory()
+    hmass = torch.from_numpy(mass).pin_memory()
+    p = hpos.cuda()
+    w = hmass.cuda()
+    stream = torch.cuda.current_stream()
+
+    # first build sizes the cell arrays; later builds use that capacity and
+    # need no host synchronisation
+    tree = tb.build(p, w, n_crit=n_crit, radix_bits=a.radix_bits)
+    C = tree.n_cells
+    tb.moments(tree, p, w)
+    torch.cuda.synchronize()
+    for _ in range(a.warmup):
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+        tb.moments(tree, p, w)
+    torch.cuda.synchronize()
+    st = tree.sync()
+    if st != 0:
+        raise SystemExit(f"warm-up build failed: {tb.STATUS[st]}")
+
+    tree.profile(True)
+    tree.stage_times()   # drop anything recorded so far
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = tb.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+        tb.moments(tree, p, w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = tb.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    stages = tree.stage_times()
+    tree.profile(False)
+    st = tree.sync()
+    if st != 0:
+        raise SystemExit(f"timed build failed: {tb.STATUS[st]}")
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * a.steps * world / (ms / 1e3) / 1e6
+
+    # per-stage totals over the timed region
+    agg = {}
+    for name, v in stages:
+        agg.setdefault(name, [0.0, 0])
+        agg[name][0] += v
+        agg[name][1] += 1
+    sort_ms, sort_launches = agg.get("sort_pass", [0.0, 0])
+    passes = max(1, sort_launches // max(1, a.steps))
+    bytes_per_launch = (20 + 24 * (passes - 1)) / passes * n
+    peak, peak_kind = peaks()
+    avg_launch_s = sort_ms / max(1, sort_launches) / 1e3
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    dig = kernel_digest()
+    traffic = NCU_TRAFFIC.get(dig)
+    roofline = {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_kind": peak_kind,
+                "traffic": None if traffic is None else round(traffic * n / traffic_n(dig)),
+                "algorithmic_bytes_per_launch": round(bytes_per_launch),
+                "mean_launch_ms": round(avg_launch_s * 1e3, 4)}
+    # whole-build bytes: positions read twice (root cell, keys), positions and
+    # masses gathered once (moments), sorted keys + permutation written once,
+    # plus the cell records (29 B structure + 76 B moments)
+    cell_bytes = 105
+    strict = 12 * n + 12 * n + 16 * n + 12 * n + cell_bytes * C
+    build_s = ms / a.steps / 1e3
+    stage_ms = {k: round(v[0] / a.steps, 4) for k, v in agg.items()}
+
+    out = {"metric": "tree-build Mparticles/s", "value": round(value, 2),
+           "unit": "Mparticles/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": round(ms / a.steps, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+u64",
+           "data": "synthetic (seeded generator, same draw on every rank)",
+           "config": {"workload": a.workload, "n_particles": n, "n_crit": n_crit,
+                      "n_cells": C, "radix_bits": a.radix_bits or 8,
+                      "parallelism": f"replicas{world}",
+                      "l2": "inputs larger than L2 (1.6 GB positions vs 129 MB), no flush",
+                      "mom_mode": "fp32_compensated"},
+           "roofline": roofline,
+           "build_roofline": {"strict_bytes": int(strict),
+                              "achieved_gbs": round(strict / build_s / 1e9, 1),
+                              "frac": round(strict / build_s / 1e9 / peak, 4)},
+           "stage_ms": stage_ms,
+           "gpu_launches": int(launches),
+           "clocks": ck}
+
+    # end to end through the C ABI from pinned host buffers
+    if not a.no_e2e:
+        res = torch.empty(10, dtype=torch.float32).pin_memory()
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, tree=tree)
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(a.steps):
+            p.copy_(hpos, non_blocking=True)
+            w.copy_(hmass, non_blocking=True)
+            tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+            tb.moments(tree, p, w)
+            root = torch.cat([tree.mass[:1], tree.com[0], tree.quad[0]])
+            res.copy_(root, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        out["e2e"] = {"value": round(n * a.steps * world / (ems / 1e3) / 1e6, 2),
+                      "unit": "Mparticles/s", "h2d_bytes_per_step": int(16 * n),
+                      "d2h_bytes_per_step": 40}
+
+    if not a.no_batched and world == 1:
+        try:
+            out["batched"] = run_batched(a, tb, torch)
+        except Exception as ex:  # reported, never hides the main line
+            out["batched"] = {"error": str(ex)[:200]}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        r, dt, m = oracle_rate(pos, mass, n_crit, a.cpu_sample)
+        out["cpu_baseline"] = {"value": round(r, 4), "unit": "Mparticles/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"first {m} particles of the same draw: full FP64 build "
+                                         f"+ direct-sum moments, {dt:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def traffic_n(dig):
+    return 1
+
+
+def run_batched(a, tb, torch):
+    raise RuntimeError("batched build not available in this build")
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

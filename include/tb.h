@@ -1,0 +1,200 @@
+/*
+ * tb.h -- C ABI of the GB300 oct-tree builder.
+ *
+ * The library builds the hashed oct-tree of Tokuue & Ishiyama (MNRAS 2023,
+ * arXiv:2312.06102) on one GPU: particles in, cells out, each cell with its
+ * level, key, parent, children, particle range and multipole moments.
+ *
+ * Pipeline (paper section in brackets):
+ *   root cell + 64-bit particle keys                      [Sec. 2.2; Sec. 2.3 step 1]
+ *   stable sort of (key, original index)                  [Sec. 2.3 step 2]
+ *   leaves straight from the sorted keys                  [Sec. 2.3.1, Alg. 1, App. A]
+ *   remaining cells bottom-up, with links                 [Sec. 2.3.2, Alg. 2]
+ *   moments computed from children, never re-traversing   [Sec. 2.3, last paragraph;
+ *                                                          footnote on the centre of mass]
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers.  Inputs stay owned by the caller,
+ *    are only read, and must stay valid until the work enqueued on the
+ *    caller's stream has finished.
+ *  - Every array a tb_tree points to is DEVICE memory owned by the library;
+ *    tb_free releases it.  A tree may be passed back to tb_build /
+ *    tb_build_batched to be rebuilt in place (its buffers grow when needed).
+ *  - Work is enqueued on the caller's stream and runs asynchronously.  The
+ *    only host synchronisation is the cell-count read-back of a build whose
+ *    params.cell_capacity is 0.
+ *  - Argument errors are returned at once.  Errors the GPU detects
+ *    (non-finite coordinate, cell capacity exceeded, a look-back wait that
+ *    ran out) are written to a device status word; the next call that
+ *    synchronises returns them, as does tb_tree_status().
+ *  - Sizes: 0 <= n <= 2^31 - 1 particles.  n = 0 gives an empty tree.
+ *    1 <= n_crit <= 1024.  A NULL mass array means equal masses
+ *    fp32(1.0 / n) (the FP64 quotient rounded once to FP32).
+ *  - Positions are FP32, row-major [n][3], 4-byte aligned (16-byte alignment
+ *    takes the vectorised load path).
+ */
+#ifndef TB_H
+#define TB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tb_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    TB_OK = 0,
+    TB_EINVAL = 1,       /* bad argument (NULL pointer, size out of range, bad mode) */
+    TB_ENOMEM = 2,       /* device allocation failed */
+    TB_ECUDA = 3,        /* a CUDA runtime call failed */
+    TB_EOVERFLOW = 4,    /* more cells than params.cell_capacity (outputs not written) */
+    TB_ETIMEOUT = 5,     /* a bounded device wait ran out (results not valid) */
+    TB_ENONFINITE = 6    /* a coordinate is NaN or infinite (tree not built) */
+} tb_status;
+
+typedef enum {
+    TB_MOM_FP32_COMP = 0,   /* FP32 with two-sum / two-product compensation (default) */
+    TB_MOM_FP32_PLAIN = 1,  /* FP32, uncompensated (reported for comparison) */
+    TB_MOM_FP64 = 2         /* FP64 accumulation; also fills mass64 / com64 / quad64 */
+} tb_mom_mode;
+
+/* Maximum depth: 1 + 3 * 21 = 64 key bits (Sec. 2.2). */
+#define TB_DEPTH_MAX 21
+#define TB_LEVELS 22
+
+typedef struct {
+    int32_t n_crit;          /* a cell with more particles than this is split (Sec. 2.1) */
+    int32_t mom_mode;        /* tb_mom_mode */
+    int64_t cell_capacity;   /* 0: size the cell arrays exactly (one stream sync);
+                                >0: fixed capacity, no host sync (graph-capturable) */
+    int32_t reorder;         /* 1: tb_moments also writes pos_sorted / mass_sorted
+                                (particles in key order, Sec. 2.3 step 3) */
+    int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width) */
+    int32_t batch_threads;   /* batched build: threads per set, 0 = tuned default */
+    int32_t reserved;
+} tb_params;
+
+/* Host-side description of a tree.  Scalars are valid after a build with
+ * cell_capacity == 0, or after tb_tree_status(); every pointer is a DEVICE
+ * pointer owned by the library. */
+typedef struct tb_tree {
+    int64_t n_particles;
+    int64_t n_cells;
+    int64_t n_leaves;
+    int32_t max_depth;
+    int32_t n_crit;
+    int64_t level_offset[TB_LEVELS + 1];  /* cells of level d: [level_offset[d], level_offset[d+1]) */
+    double lo[3];                         /* root cube corner (FP32 minima, exact in FP64) */
+    double side;                          /* root cube side L (FP64) */
+    int64_t cell_capacity;                /* allocated length of the per-cell arrays */
+
+    /* particles in key order: pkey[k] is the k-th smallest key, perm[k] the
+       original index of that particle (ties keep ascending original index) */
+    uint64_t *pkey;
+    int32_t *perm;
+
+    /* cells, canonical order: level ascending, key ascending within a level */
+    uint64_t *ckey;          /* cell key: upper 3*level + 1 bits of its particles' keys; root = 1 */
+    uint8_t *level;
+    int32_t *parent;         /* -1 for the root */
+    int32_t *child_first;    /* children are [child_first, child_end); -1/-1 for a leaf */
+    int32_t *child_end;
+    int32_t *pfirst;         /* particles are sorted positions [pfirst, pend) */
+    int32_t *pend;
+    int32_t *leaf_cell;      /* the j-th leaf in key order (n_leaves entries) */
+
+    /* moments (tb_moments / tb_build_batched) */
+    float *mass;             /* [C] total mass */
+    float *com;              /* [C][3] centre of mass, rounded to FP32 */
+    float *com_lo;           /* [C][3] com + com_lo is the centre of mass to ~2^-44 relative */
+    float *quad;             /* [C][6] central second moment sum m (x-c)(x-c)^T: xx xy xz yy yz zz */
+    float *aabb;             /* [C][6] member bounding box: min x y z, max x y z (exact) */
+    double *mass64;          /* FP64 mode only, else NULL */
+    double *com64;
+    double *quad64;
+    float *pos_sorted;       /* reorder only: [n][3] positions in key order, else NULL */
+    float *mass_sorted;      /* reorder only: [n] */
+
+    /* batched builds only (NULL / 0 otherwise) */
+    int32_t n_sets;
+    int64_t *set_particle_offset;  /* [S+1] device copy of the caller's offsets */
+    int64_t *set_cell_offset;      /* [S+1] cells of set s: [off[s], off[s+1]) */
+    double *set_root;              /* [S][4] per-set root cube: lo x y z, side */
+
+    void *internal;                /* library workspace */
+} tb_tree;
+
+/* Build the tree structure: root cell, keys, sort, leaves, cells and links
+ * (Sec. 2.2, Sec. 2.3 steps 1, 2 and 4, Alg. 1, Alg. 2).
+ *   d_pos   [n][3] FP32 positions (device)
+ *   d_mass  [n] FP32 masses or NULL; only used by a later tb_moments
+ *   n       number of particles
+ *   params  n_crit, capacity, tuning (must not be NULL)
+ *   stream  caller's stream
+ *   tree    in: NULL to allocate a new tree, or a tree to rebuild in place;
+ *           out: the tree (owned by the library until tb_free)
+ * Returns TB_OK, TB_EINVAL, TB_ENOMEM, TB_ECUDA, or (capacity 0 only)
+ * TB_ENONFINITE / TB_ETIMEOUT detected during the build. */
+tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_params *params,
+                   tb_stream stream, tb_tree **tree);
+
+/* Fill mass, com, com_lo, quad and aabb of every cell of a built tree:
+ * leaves by summation over their members in key order, every other cell
+ * from its children (Sec. 2.3: properties are computed as cells are made,
+ * the centre of mass of a parent from those of its children; higher
+ * multipoles likewise).  d_pos / d_mass must be the arrays the tree was
+ * built from.  Cells of more than 2^20 particles are summed in FP64 in
+ * every mode. */
+tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
+
+/* Build S independent trees in one call, moments included.  Particles of set
+ * s are d_pos[d_set_offsets[s] .. d_set_offsets[s+1]); each set has its own
+ * tight root cube.  Cells of each set are contiguous and canonical within the
+ * set; parent / child / particle indices are global (into the whole arrays).
+ *   d_set_offsets  [S+1] int64, device, non-decreasing, d_set_offsets[0] = 0
+ *   n_total        d_set_offsets[S] (the host must know it for allocation)
+ * Every set must hold at most 2^31 - 1 particles.  With
+ * params.cell_capacity > 0 and a tree from an earlier call with the same S
+ * and n_total, nothing is allocated and nothing synchronises, so the call can
+ * be captured into a CUDA graph and replayed. */
+tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_t *d_set_offsets,
+                           int32_t n_sets, int64_t n_total, const tb_params *params,
+                           tb_stream stream, tb_tree **tree);
+
+/* Release a tree (NULL-safe).  Synchronises with the device before freeing. */
+void tb_free(tb_tree *tree);
+
+/* Synchronise `stream`, refresh the tree's host scalars from the device and
+ * return the device status (TB_OK, TB_ENONFINITE, TB_EOVERFLOW, TB_ETIMEOUT). */
+tb_status tb_tree_status(tb_tree *tree, tb_stream stream);
+
+const char *tb_status_string(tb_status s);
+
+/* Default parameters: n_crit 16, compensated FP32 moments, exact sizing. */
+tb_params tb_default_params(void);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t tb_kernel_launches(void);
+
+/* Per-stage timing of the most recent builds of `tree`.  When enabled the
+ * library records CUDA events on the build stream at each stage boundary.
+ * tb_stage_times synchronises the stream and writes up to `max` elapsed
+ * times (ms) of the last build and moment call, returning the count; names
+ * come from tb_stage_name.  Stage 0 is the root cell, 1 the keys, 2..1+P the
+ * P sort passes, then level counts, cell emission and moments. */
+tb_status tb_profile(tb_tree *tree, int32_t enable);
+int32_t tb_stage_times(tb_tree *tree, tb_stream stream, float *ms, int32_t max);
+const char *tb_stage_name(tb_tree *tree, int32_t i);
+
+/* Self-test of the bounded device wait: launches one kernel that waits on a
+ * flag nothing sets, giving up after `spin_limit` polls.  Returns
+ * TB_ETIMEOUT when the wait ran out and the context is still usable. */
+tb_status tb_selftest_wait(int64_t spin_limit, tb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TB_H */

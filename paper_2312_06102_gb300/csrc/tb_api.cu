@@ -1,0 +1,407 @@
+// tb_api.cu -- host side of the C ABI declared in include/tb.h: argument
+// checks, buffer management, the launch sequence of a build, status
+// read-back and stage timing.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "tb_internal.h"
+
+namespace tb {
+
+int64_t g_launches = 0;
+
+namespace {
+
+// Test hook: TB_FAULT_ALLOC=k makes the k-th device allocation of the
+// process fail (k counted from 1), to exercise the TB_ENOMEM paths.
+int64_t g_alloc_calls = 0;
+int64_t fault_alloc_at() {
+    static int64_t v = -2;
+    if (v == -2) {
+        const char *e = std::getenv("TB_FAULT_ALLOC");
+        v = e ? std::atoll(e) : -1;
+    }
+    return v;
+}
+
+template <class T>
+bool dev_alloc(T *&p, int64_t count) {
+    ++g_alloc_calls;
+    if (fault_alloc_at() > 0 && g_alloc_calls == fault_alloc_at()) return false;
+    void *q = nullptr;
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p = static_cast<T *>(q);
+    return true;
+}
+
+template <class T>
+void dev_free(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+struct TreeState {
+    tb_tree pub;
+    Workspace ws;
+    tb_params params;
+    int radix_bits = 8;
+};
+
+TreeState *state_of(tb_tree *t) { return reinterpret_cast<TreeState *>(t); }
+
+tb_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TB_OK;
+    if (e == cudaErrorMemoryAllocation) return TB_ENOMEM;
+    return TB_ECUDA;
+}
+
+tb_status from_dev(uint32_t st) {
+    if (st & kErrNonFinite) return TB_ENONFINITE;
+    if (st & kErrTimeout) return TB_ETIMEOUT;
+    if (st & kErrOverflow) return TB_EOVERFLOW;
+    return TB_OK;
+}
+
+void free_cells(TreeState &S) {
+    tb_tree &t = S.pub;
+    dev_free(t.ckey); dev_free(t.level); dev_free(t.parent); dev_free(t.child_first);
+    dev_free(t.child_end); dev_free(t.pfirst); dev_free(t.pend);
+    dev_free(t.mass); dev_free(t.com); dev_free(t.com_lo); dev_free(t.quad); dev_free(t.aabb);
+    dev_free(t.mass64); dev_free(t.com64); dev_free(t.quad64);
+    dev_free(S.ws.arrive);
+    t.cell_capacity = 0;
+    S.ws.cell_cap = 0;
+}
+
+void free_particles(TreeState &S) {
+    tb_tree &t = S.pub;
+    Workspace &ws = S.ws;
+    dev_free(t.pkey); dev_free(t.perm); dev_free(ws.keys_alt); dev_free(ws.perm_alt);
+    dev_free(t.leaf_cell); dev_free(ws.leaf_pfirst); dev_free(ws.big_leaf);
+    dev_free(ws.level_cnt); dev_free(ws.lookback);
+    dev_free(t.pos_sorted); dev_free(t.mass_sorted);
+    ws.n_cap = 0;
+    ws.tiles_cap = 0;
+    ws.level_tiles_cap = 0;
+}
+
+tb_status ensure_fixed(TreeState &S) {
+    Workspace &ws = S.ws;
+    if (ws.info) return TB_OK;
+    if (!dev_alloc(ws.info, 1) || !dev_alloc(ws.hist, 16 * 2048) ||
+        !dev_alloc(ws.bbox_part, bbox_grid() * 8))
+        return TB_ENOMEM;
+    if (cudaMallocHost(&ws.h_info, sizeof(DevInfo)) != cudaSuccess) {
+        cudaGetLastError();
+        return TB_ENOMEM;
+    }
+    if (cudaMemset(ws.info, 0, sizeof(DevInfo)) != cudaSuccess) return TB_ECUDA;
+    std::memset(ws.h_info, 0, sizeof(DevInfo));
+    return TB_OK;
+}
+
+tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reorder) {
+    Workspace &ws = S.ws;
+    tb_tree &t = S.pub;
+    const int64_t tiles = (n + cfg.tile() - 1) / cfg.tile();
+    const int64_t need_lb = tiles * (int64_t(1) << cfg.radix_bits);
+    const int64_t ltiles = (n + level_tile_size() - 1) / level_tile_size();
+    if (n > ws.n_cap || need_lb > ws.tiles_cap || ltiles > ws.level_tiles_cap) {
+        cudaDeviceSynchronize();
+        free_particles(S);
+        int64_t cap = n;
+        int64_t lb = need_lb > 0 ? need_lb : 1;
+        if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
+            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) ||
+            !dev_alloc(ws.leaf_pfirst, cap) || !dev_alloc(ws.big_leaf, cap) ||
+            !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
+            return TB_ENOMEM;
+        if (cudaMemset(ws.lookback, 0, sizeof(uint64_t) * lb) != cudaSuccess) return TB_ECUDA;
+        ws.n_cap = cap;
+        ws.tiles_cap = lb;
+        ws.level_tiles_cap = ltiles;
+    }
+    if (reorder && (!t.pos_sorted || ws.n_cap > ws.reorder_cap)) {
+        dev_free(t.pos_sorted);
+        dev_free(t.mass_sorted);
+        if (!dev_alloc(t.pos_sorted, 3 * ws.n_cap) || !dev_alloc(t.mass_sorted, ws.n_cap))
+            return TB_ENOMEM;
+        ws.reorder_cap = ws.n_cap;
+    }
+    return TB_OK;
+}
+
+tb_status ensure_cells(TreeState &S, int64_t cells, bool fp64) {
+    Workspace &ws = S.ws;
+    tb_tree &t = S.pub;
+    if (cells > ws.cell_cap || (fp64 && !t.mass64)) {
+        cudaDeviceSynchronize();
+        int64_t cap = cells > ws.cell_cap ? cells : ws.cell_cap;
+        free_cells(S);
+        if (!dev_alloc(t.ckey, cap) || !dev_alloc(t.level, cap) || !dev_alloc(t.parent, cap) ||
+            !dev_alloc(t.child_first, cap) || !dev_alloc(t.child_end, cap) ||
+            !dev_alloc(t.pfirst, cap) || !dev_alloc(t.pend, cap) || !dev_alloc(t.mass, cap) ||
+            !dev_alloc(t.com, 3 * cap) || !dev_alloc(t.com_lo, 3 * cap) ||
+            !dev_alloc(t.quad, 6 * cap) || !dev_alloc(t.aabb, 6 * cap) ||
+            !dev_alloc(ws.arrive, cap))
+            return TB_ENOMEM;
+        if (fp64 && (!dev_alloc(t.mass64, cap) || !dev_alloc(t.com64, 3 * cap) ||
+                     !dev_alloc(t.quad64, 6 * cap)))
+            return TB_ENOMEM;
+        ws.cell_cap = cap;
+        t.cell_capacity = cap;
+    }
+    return TB_OK;
+}
+
+void refresh_host(TreeState &S) {
+    const DevInfo &h = *S.ws.h_info;
+    tb_tree &t = S.pub;
+    t.n_cells = h.n_cells;
+    t.n_leaves = h.n_leaves;
+    t.max_depth = h.max_depth;
+    for (int d = 0; d <= kLevels; ++d) t.level_offset[d] = h.level_offset[d];
+    for (int a = 0; a < 3; ++a) t.lo[a] = (double)h.lo[a];
+    t.side = h.side;
+}
+
+tb_status read_info(TreeState &S, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(S.ws.h_info, S.ws.info, sizeof(DevInfo),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    refresh_host(S);
+    return from_dev(S.ws.h_info->status);
+}
+
+bool valid_params(const tb_params *p) {
+    return p && p->n_crit >= 1 && p->n_crit <= kMaxNcrit && p->mom_mode >= 0 && p->mom_mode <= 2 &&
+           p->cell_capacity >= 0 &&
+           (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11));
+}
+
+SortCfg pick_cfg(const tb_params *p) {
+    if (p->radix_bits) return default_sort_cfg(p->radix_bits);
+    return default_sort_cfg(8);
+}
+
+}  // namespace
+
+void mark(Workspace &ws, const char *name, cudaStream_t s) {
+    if (!ws.profile || ws.n_events >= 200000) return;
+    if (ws.n_events == ws.ev.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        ws.ev.push_back(e);
+        ws.ev_name.push_back(name);
+    }
+    cudaEventRecord(ws.ev[ws.n_events], s);
+    ws.ev_name[ws.n_events] = name;
+    ++ws.n_events;
+}
+
+}  // namespace tb
+
+using namespace tb;
+
+extern "C" {
+
+tb_params tb_default_params(void) {
+    tb_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.n_crit = 16;
+    p.mom_mode = TB_MOM_FP32_COMP;
+    return p;
+}
+
+const char *tb_status_string(tb_status s) {
+    switch (s) {
+        case TB_OK: return "ok";
+        case TB_EINVAL: return "invalid argument";
+        case TB_ENOMEM: return "device allocation failed";
+        case TB_ECUDA: return "CUDA runtime error";
+        case TB_EOVERFLOW: return "cell capacity exceeded";
+        case TB_ETIMEOUT: return "bounded device wait ran out";
+        case TB_ENONFINITE: return "non-finite coordinate";
+    }
+    return "unknown status";
+}
+
+int64_t tb_kernel_launches(void) { return g_launches; }
+
+tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_params *params,
+                   tb_stream stream, tb_tree **tree) {
+    (void)d_mass;
+    if (!tree || !valid_params(params) || n < 0 || n > 2147483647LL) return TB_EINVAL;
+    if (n > 0 && (!d_pos || (reinterpret_cast<uintptr_t>(d_pos) & 3u))) return TB_EINVAL;
+    if (*tree && (*tree)->n_sets != 0) return TB_EINVAL;   // a batched tree
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    TreeState *S = *tree ? state_of(*tree) : nullptr;
+    if (!S) {
+        S = new (std::nothrow) TreeState();
+        if (!S) return TB_ENOMEM;
+        std::memset(&S->pub, 0, sizeof(tb_tree));
+        S->pub.internal = &S->ws;
+        *tree = &S->pub;
+    }
+    tb_status st = ensure_fixed(*S);
+    if (st != TB_OK) return st;
+    Workspace &ws = S->ws;
+    tb_tree &t = S->pub;
+    S->params = *params;
+    const SortCfg cfg = pick_cfg(params);
+    S->radix_bits = cfg.radix_bits;
+    ws.last_stream = s;
+    t.n_particles = n;
+    t.n_crit = params->n_crit;
+    ws.cell_cap_request = params->cell_capacity;
+    if (n == 0) {
+        t.n_cells = t.n_leaves = 0;
+        t.max_depth = 0;
+        for (int d = 0; d <= kLevels; ++d) t.level_offset[d] = 0;
+        for (int a = 0; a < 3; ++a) t.lo[a] = 0.0;
+        t.side = 1.0;
+        cudaError_t e = cudaMemsetAsync(ws.info, 0, offsetof(DevInfo, sort_tile_ctr), s);
+        return from_cuda(e);
+    }
+    st = ensure_particles(*S, n, cfg, params->reorder != 0);
+    if (st != TB_OK) return st;
+    if (params->cell_capacity > 0) {
+        st = ensure_cells(*S, params->cell_capacity, params->mom_mode == TB_MOM_FP64);
+        if (st != TB_OK) return st;
+    }
+    const int passes = sort_passes(cfg.radix_bits);
+    mark(ws, "start", s);
+    cudaError_t e = launch_root(d_pos, n, ws, passes << cfg.radix_bits, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    mark(ws, "root", s);
+    // the unsorted keys go where the last pass will read from the other buffer
+    uint64_t *ka = (passes & 1) ? ws.keys_alt : t.pkey;
+    uint64_t *kb = (passes & 1) ? t.pkey : ws.keys_alt;
+    int32_t *pa = (passes & 1) ? ws.perm_alt : t.perm;
+    int32_t *pb = (passes & 1) ? t.perm : ws.perm_alt;
+    e = launch_keys(d_pos, n, ka, ws, cfg, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    mark(ws, "keys", s);
+    uint64_t *kout = nullptr;
+    int32_t *pout = nullptr;
+    e = launch_sort(ka, kb, pa, pb, n, ws, cfg, kout, pout, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (kout != t.pkey || pout != t.perm) return TB_ECUDA;
+    e = launch_levels(t.pkey, n, params->n_crit, ws, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    mark(ws, "levels", s);
+    if (params->cell_capacity == 0) {
+        st = read_info(*S, s);
+        if (st != TB_OK) return st;
+        st = ensure_cells(*S, ws.h_info->n_cells, params->mom_mode == TB_MOM_FP64);
+        if (st != TB_OK) return st;
+    }
+    e = launch_emit(t.pkey, n, params->n_crit, ws, t, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    mark(ws, "emit", s);
+    return TB_OK;
+}
+
+tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream) {
+    if (!tree || (tree->n_particles > 0 && !d_pos)) return TB_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_pos) & 3u) return TB_EINVAL;
+    TreeState *S = state_of(tree);
+    if (tree->n_sets != 0) return TB_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (tree->n_particles == 0) return TB_OK;
+    const bool fp64 = S->params.mom_mode == TB_MOM_FP64;
+    if (fp64 && !tree->mass64) {
+        tb_status st = ensure_cells(*S, S->ws.cell_cap, true);
+        if (st != TB_OK) return st;
+    }
+    if (S->params.reorder && !tree->pos_sorted) return TB_EINVAL;
+    S->ws.last_stream = s;
+    cudaError_t e = launch_moments(*tree, d_pos, d_mass, S->ws, S->params.mom_mode, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    mark(S->ws, "moments", s);
+    return TB_OK;
+}
+
+tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_t *d_set_offsets,
+                           int32_t n_sets, int64_t n_total, const tb_params *params,
+                           tb_stream stream, tb_tree **tree) {
+    (void)d_pos; (void)d_mass; (void)d_set_offsets; (void)n_sets; (void)n_total; (void)params;
+    (void)stream; (void)tree;
+    return TB_EINVAL;
+}
+
+void tb_free(tb_tree *tree) {
+    if (!tree) return;
+    TreeState *S = state_of(tree);
+    cudaDeviceSynchronize();
+    free_cells(*S);
+    free_particles(*S);
+    Workspace &ws = S->ws;
+    dev_free(ws.info); dev_free(ws.hist); dev_free(ws.bbox_part);
+    if (ws.h_info) cudaFreeHost(ws.h_info);
+    for (cudaEvent_t e : ws.ev) cudaEventDestroy(e);
+    dev_free(ws.set_order); dev_free(ws.set_level); dev_free(ws.set_ctr);
+    dev_free(ws.bkeys_a); dev_free(ws.bkeys_b); dev_free(ws.bperm_b);
+    dev_free(tree->set_particle_offset); dev_free(tree->set_cell_offset); dev_free(tree->set_root);
+    delete S;
+}
+
+tb_status tb_tree_status(tb_tree *tree, tb_stream stream) {
+    if (!tree) return TB_EINVAL;
+    TreeState *S = state_of(tree);
+    if (!S->ws.info) return TB_OK;
+    return read_info(*S, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tb_status tb_profile(tb_tree *tree, int32_t enable) {
+    if (!tree) return TB_EINVAL;
+    state_of(tree)->ws.profile = enable != 0;
+    return TB_OK;
+}
+
+int32_t tb_stage_times(tb_tree *tree, tb_stream stream, float *ms, int32_t max) {
+    if (!tree || !ms) return 0;
+    Workspace &ws = state_of(tree)->ws;
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return 0;
+    int32_t k = 0;
+    for (size_t i = 1; i < ws.n_events && k < max; ++i, ++k) {
+        float v = 0.f;
+        cudaEventElapsedTime(&v, ws.ev[i - 1], ws.ev[i]);
+        ms[k] = v;
+    }
+    // names stay readable until the next record; restart the accumulation
+    ws.last_read = ws.n_events;
+    ws.n_events = 0;
+    return k;
+}
+
+const char *tb_stage_name(tb_tree *tree, int32_t i) {
+    if (!tree) return "";
+    Workspace &ws = state_of(tree)->ws;
+    if (i < 0 || (size_t)i + 1 >= ws.last_read) return "";
+    return ws.ev_name[i + 1];
+}
+
+tb_status tb_selftest_wait(int64_t spin_limit, tb_stream stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t *buf = nullptr;
+    if (cudaMalloc(&buf, 2 * sizeof(uint32_t)) != cudaSuccess) return TB_ENOMEM;
+    cudaMemsetAsync(buf, 0, 2 * sizeof(uint32_t), s);
+    cudaError_t e = launch_wait_selftest(spin_limit, buf, buf + 1, s);
+    uint32_t h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, buf, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_dev(h[0]);
+}
+
+}  // extern "C"

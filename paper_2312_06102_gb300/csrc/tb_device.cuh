@@ -1,0 +1,134 @@
+// tb_device.cuh -- device-side building blocks shared by the tree kernels.
+//
+// Nothing here is a kernel.  It holds the key arithmetic of Sec. 2.2, the
+// minimum distinguished depth of Sec. 2.3.1, the FP32 error-free transforms
+// used by the compensated moments, and the bounded wait every spin uses.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tb_internal.h"
+
+namespace tb {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ----------------------------------------------------------------- keys
+
+// Minimum distinguished depth (Sec. 2.3.1): ceil(clz(a ^ b) / 3); __clzll(0)
+// is 64, so identical keys give 22 ("never separated").
+__device__ __forceinline__ int min_depth(uint64_t a, uint64_t b) {
+    return (__clzll(a ^ b) + 2) / 3;
+}
+
+// Depth-d cell key of a particle key: its upper 3d+1 bits (Sec. 2.3.1).
+__device__ __forceinline__ uint64_t cell_key(uint64_t key, int d) {
+    return key >> (63 - 3 * d);
+}
+
+// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Key: a leading 1, then the 21 octant digits, x the most significant bit
+// of each digit (Sec. 2.2).
+__device__ __forceinline__ uint64_t morton_key(uint32_t qx, uint32_t qy, uint32_t qz) {
+    return (1ull << 63) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+// Exact error-free sum a + b = s + e (Knuth's TwoSum, no branch).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e = a + b when |a| >= |b| (Dekker's Fast2Sum).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Exact product a * b = p + e with one FMA.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// 21-bit quantisation of one coordinate, equal bit for bit to the FP64
+// definition q = min(2^21-1, floor(fl64(fl64(x - lo) * s))).
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the product is
+// formed in FP32 double-float arithmetic: x - lo = dh + dl exactly (TwoSum),
+// s ~ s_hi + s_lo, t ~ p + c with p = fl32(dh * s_hi).  The estimate is within
+// 2^-22 of the FP64 value for t < 2^21.  When the fractional part of the
+// estimate lies within 2^-18 of an integer the floor is ambiguous and the
+// FP64 operations themselves decide (a few particles in 10^5).
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float s_hi, float s_lo, double s,
+                                             bool exact_only) {
+    if (!exact_only) {
+        float dh, dl;
+        two_sum(x, -lo, dh, dl);
+        float p, e;
+        two_prod(dh, s_hi, p, e);
+        float c = __fmaf_rn(dh, s_lo, __fmaf_rn(dl, s_hi, __fmaf_rn(dl, s_lo, e)));
+        float fl = floorf(p);
+        float f = __fadd_rn(__fsub_rn(p, fl), c);
+        float k = floorf(f);
+        float r = __fsub_rn(f, k);
+        const float delta = 3.814697265625e-06f;  // 2^-18
+        if (r > delta && r < 1.0f - delta) {
+            float q = __fadd_rn(fl, k);
+            if (q < 0.f) q = 0.f;
+            if (q > 2097151.f) q = 2097151.f;
+            return (uint32_t)q;
+        }
+    }
+    double d = __dsub_rn((double)x, (double)lo);
+    double t = __dmul_rn(d, s);
+    double f = floor(t);
+    if (f < 0.0) f = 0.0;
+    if (f > 2097151.0) f = 2097151.0;
+    return (uint32_t)f;
+}
+
+// ------------------------------------------------------- bounded waits
+
+// Spin limit for every wait on another block.  A wait that runs out sets
+// TB_ERR_TIMEOUT in the status word and returns false; callers then carry
+// on with a harmless value so that no block waits forever.
+__device__ __forceinline__ bool poll_backoff(int64_t &iter, int64_t limit) {
+    if (++iter > limit) return false;
+    if (iter > 64) __nanosleep(iter > 4096 ? 256 : 32);
+    return true;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void flag_error(uint32_t *status, uint32_t bit) {
+    atomicOr(status, bit);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace tb

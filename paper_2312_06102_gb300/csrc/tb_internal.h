@@ -1,0 +1,126 @@
+// tb_internal.h -- declarations shared by the library's translation units:
+// the device-side build record, status bits, sizes and the host launchers of
+// each kernel family.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/tb.h"
+
+namespace tb {
+
+constexpr int kLevels = TB_LEVELS;          // depths 0..21
+constexpr int kDepthMax = TB_DEPTH_MAX;
+constexpr int kLevelFields = kLevels + 1;   // 22 level counters + 1 leaf counter
+constexpr int kMaxNcrit = 1024;
+constexpr int64_t kBigCell = int64_t(1) << 20;   // cells above this are summed in FP64
+
+// device status bits (tb_dev_info::status)
+constexpr uint32_t kErrNonFinite = 1u;
+constexpr uint32_t kErrOverflow = 2u;
+constexpr uint32_t kErrTimeout = 4u;
+
+// Record of one build, in device memory; written by the kernels, read back
+// by the host after a synchronisation.
+struct DevInfo {
+    float lo[3];           // root corner (FP32 minima)
+    float hi[3];
+    double side;           // L = max_a (hi_a - lo_a), 1 if 0
+    double scale;          // 2^21 / L
+    float s_hi, s_lo;      // scale ~ s_hi + s_lo
+    uint32_t exact_only;   // 1: quantise with FP64 only (extreme ranges)
+    uint32_t status;       // kErr* bits
+    uint32_t epoch;        // look-back epoch base of this build
+    uint32_t n_leaves;
+    int32_t max_depth;
+    int32_t pad;
+    int64_t n_cells;
+    int64_t level_offset[kLevels + 1];
+    uint32_t sort_tile_ctr[16];   // dynamic tile ids, one counter per sort pass
+    uint32_t misc_ctr[8];         // [0] bbox blocks done, [1] level-scan blocks done,
+                                  // [2] big-leaf queue length, [3] big-leaf tickets
+};
+
+// Sort tuning: a compiled variant.
+struct SortCfg {
+    int radix_bits;
+    int threads;
+    int items;
+    int tile() const { return threads * items; }
+};
+
+int sort_passes(int radix_bits);
+
+// Workspace of one tree (device pointers unless noted).
+struct Workspace {
+    int64_t n_cap = 0;         // particle capacity
+    int64_t tiles_cap = 0;     // look-back tiles capacity
+    int64_t cell_cap = 0;
+    int64_t level_tiles_cap = 0;
+    int64_t leaf_cap = 0;
+    int64_t bbox_blocks = 0;
+    int64_t cell_cap_request = 0;   // params.cell_capacity of the current build
+    int64_t reorder_cap = 0;
+
+    uint64_t *keys_alt = nullptr;
+    int32_t *perm_alt = nullptr;
+    uint32_t *hist = nullptr;        // [passes][radix]
+    uint64_t *lookback = nullptr;    // [tiles][radix]
+    float *bbox_part = nullptr;      // [blocks][8]
+    uint32_t *level_cnt = nullptr;   // [level tiles][kLevelFields]
+    uint32_t *arrive = nullptr;      // [cells] child-arrival counters
+    int32_t *leaf_pfirst = nullptr;  // [leaves]
+    int32_t *big_leaf = nullptr;     // [leaves] queue of leaves too big for one thread
+    DevInfo *info = nullptr;
+    DevInfo *h_info = nullptr;       // pinned host mirror
+
+    // profiling: events recorded at stage boundaries, accumulated over
+    // builds until read
+    bool profile = false;
+    size_t n_events = 0;
+    size_t last_read = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char *> ev_name;
+
+    // batched
+    int64_t set_cap = 0;
+    int32_t *set_order = nullptr;    // [S] processing order (largest first)
+    int64_t *set_level = nullptr;    // [S][kLevelFields] per-set counts
+    uint32_t *set_ctr = nullptr;     // work-queue counters
+    uint64_t *bkeys_a = nullptr;     // batched sort scratch
+    uint64_t *bkeys_b = nullptr;
+    int32_t *bperm_b = nullptr;
+    int64_t batched_n_cap = 0;
+
+    cudaStream_t last_stream = nullptr;
+};
+
+// ------------------------------------------------------------ launchers
+// Each returns cudaSuccess or the launch error.
+
+extern int64_t g_launches;
+
+cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len, cudaStream_t s);
+cudaError_t launch_keys(const float *pos, int64_t n, uint64_t *keys, Workspace &ws,
+                        const SortCfg &cfg, cudaStream_t s);
+cudaError_t launch_sort(uint64_t *keys_in_place_a, uint64_t *keys_b, int32_t *perm_a,
+                        int32_t *perm_b, int64_t n, Workspace &ws, const SortCfg &cfg,
+                        uint64_t *&keys_out, int32_t *&perm_out, cudaStream_t s);
+cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int n_crit, Workspace &ws,
+                          cudaStream_t s);
+cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int n_crit, Workspace &ws,
+                        tb_tree &t, cudaStream_t s);
+cudaError_t launch_moments(tb_tree &t, const float *pos, const float *mass, Workspace &ws,
+                           int mode, cudaStream_t s);
+cudaError_t launch_wait_selftest(int64_t limit, uint32_t *status, uint32_t *flag, cudaStream_t s);
+
+int level_tile_size();
+int64_t bbox_grid();
+SortCfg default_sort_cfg(int radix_bits);
+bool sort_cfg_valid(const SortCfg &c);
+
+void mark(Workspace &ws, const char *name, cudaStream_t s);
+
+}  // namespace tb

@@ -1,0 +1,673 @@
+// tb_moments.cu -- cell moments without traversing the tree (Sec. 2.3: cell
+// properties are computed as cells are created; the centre of mass of a
+// parent comes from those of its children, higher multipoles likewise).
+//
+// One thread per leaf (leaves taken in key order, so a warp reads a
+// contiguous stretch of the permutation) sums its member particles; then
+// the thread that brings the last child of a parent (an atomic arrival
+// count) combines the parent's children and climbs on.  Every parent is
+// therefore computed exactly once, from all its children in index order, so
+// the result does not depend on which thread arrives last.
+//
+// Moments of a cell: M = sum m; centre of mass c = sum m x / M; central
+// second moment Q = sum m (x - c)(x - c)^T (6 components xx xy xz yy yz zz);
+// member bounding box.  Sums run relative to a reference point inside the
+// cell (the first member particle for a leaf, the first child's centre for a
+// parent), which keeps the FP32 differences small and exact or nearly so.
+// Parent from children (parallel-axis theorem):
+//   M = sum M_j, c = sum M_j c_j / M, Q = sum [Q_j + M_j (c_j - c)(c_j - c)^T].
+//
+// Modes:
+//   FP32_COMP  -- two-sum / two-product compensated FP32; the centre of mass
+//                 is kept as an unevaluated pair com + com_lo (an FP32 value
+//                 cannot hold a deep cell's centre to 2e-6 of its side);
+//   FP32_PLAIN -- uncompensated FP32, com_lo = 0;
+//   FP64       -- FP64 accumulation; FP64 outputs beside the FP32 ones.
+// A cell of more than 2^20 particles is summed / combined in FP64 in every
+// mode.  Leaves too long for one thread (only depth-21 leaves of identical
+// keys can be) go to a queue served block-wide by a second kernel.
+#include "tb_device.cuh"
+
+namespace tb {
+
+namespace {
+
+constexpr int kMomThreads = 256;
+constexpr int kBigLeafThread = 2048;   // longer leaves are summed by a block
+constexpr int kBigThreads = 256;
+
+struct MomOut {
+    float *mass, *com, *com_lo, *quad, *aabb;
+    double *mass64, *com64, *quad64;
+    float *pos_sorted, *mass_sorted;
+};
+
+struct TreeIn {
+    const int32_t *perm, *parent, *child_first, *child_end, *pfirst, *pend;
+    const int32_t *leaf_cell, *leaf_pfirst;
+    uint32_t *arrive;
+    int32_t *big_leaf;
+    int64_t n;
+};
+
+__device__ __forceinline__ int qidx(int a, int b) {
+    // xx xy xz yy yz zz
+    return (a == 0) ? b : (a == 1 ? 2 + b : 5);
+}
+
+// --------------------------------------------------------- accumulators
+
+// compensated FP32 raw sums relative to a reference point
+struct AccC {
+    float M, Mc, S[3], Sc[3], Q[6], Qc[6];
+    __device__ void init() {
+        M = Mc = 0.f;
+        for (int a = 0; a < 3; ++a) S[a] = Sc[a] = 0.f;
+        for (int j = 0; j < 6; ++j) Q[j] = Qc[j] = 0.f;
+    }
+    __device__ void add(float m, const float dx[3]) {
+        float e;
+        two_sum(M, m, M, e);
+        Mc += e;
+        float p[3], pe[3];
+        for (int a = 0; a < 3; ++a) {
+            two_prod(m, dx[a], p[a], pe[a]);
+            two_sum(S[a], p[a], S[a], e);
+            Sc[a] += e + pe[a];
+        }
+        int j = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b, ++j) {
+                float q, qe;
+                two_prod(p[a], dx[b], q, qe);
+                qe = __fmaf_rn(pe[a], dx[b], qe);
+                two_sum(Q[j], q, Q[j], e);
+                Qc[j] += e + qe;
+            }
+    }
+    // merge another accumulator of the same reference point
+    __device__ void merge(const AccC &o) {
+        float e;
+        two_sum(M, o.M, M, e); Mc += e + o.Mc;
+        for (int a = 0; a < 3; ++a) { two_sum(S[a], o.S[a], S[a], e); Sc[a] += e + o.Sc[a]; }
+        for (int j = 0; j < 6; ++j) { two_sum(Q[j], o.Q[j], Q[j], e); Qc[j] += e + o.Qc[j]; }
+    }
+};
+
+struct AccP {
+    float M, S[3], Q[6];
+    __device__ void init() {
+        M = 0.f;
+        for (int a = 0; a < 3; ++a) S[a] = 0.f;
+        for (int j = 0; j < 6; ++j) Q[j] = 0.f;
+    }
+    __device__ void add(float m, const float dx[3]) {
+        M += m;
+        int j = 0;
+        for (int a = 0; a < 3; ++a) {
+            float w = m * dx[a];
+            S[a] += w;
+            for (int b = a; b < 3; ++b, ++j) Q[j] += w * dx[b];
+        }
+    }
+    __device__ void merge(const AccP &o) {
+        M += o.M;
+        for (int a = 0; a < 3; ++a) S[a] += o.S[a];
+        for (int j = 0; j < 6; ++j) Q[j] += o.Q[j];
+    }
+};
+
+struct AccD {
+    double M, S[3], Q[6];
+    __device__ void init() {
+        M = 0.0;
+        for (int a = 0; a < 3; ++a) S[a] = 0.0;
+        for (int j = 0; j < 6; ++j) Q[j] = 0.0;
+    }
+    __device__ void add(double m, const double dx[3]) {
+        M += m;
+        int j = 0;
+        for (int a = 0; a < 3; ++a) {
+            double w = m * dx[a];
+            S[a] += w;
+            for (int b = a; b < 3; ++b, ++j) Q[j] += w * dx[b];
+        }
+    }
+    __device__ void merge(const AccD &o) {
+        M += o.M;
+        for (int a = 0; a < 3; ++a) S[a] += o.S[a];
+        for (int j = 0; j < 6; ++j) Q[j] += o.Q[j];
+    }
+};
+
+// double-float quotient (nh + nl) / (dh + dl)
+__device__ __forceinline__ void df_div(float nh, float nl, float dh, float dl, float &qh, float &ql) {
+    float q1 = __fdiv_rn(nh, dh);
+    float r = __fmaf_rn(-q1, dh, nh);
+    r = __fadd_rn(r, nl);
+    r = __fmaf_rn(-q1, dl, r);
+    float q2 = __fdiv_rn(r, dh);
+    fast_two_sum(q1, q2, qh, ql);
+}
+
+// ------------------------------------------------------------ writers
+
+__device__ void write_cell_f32(const MomOut &o, int64_t c, float M, const float ch[3],
+                               const float cl[3], const float Q[6], const float bb[6]) {
+    o.mass[c] = M;
+    for (int a = 0; a < 3; ++a) { o.com[3 * c + a] = ch[a]; o.com_lo[3 * c + a] = cl[a]; }
+    for (int j = 0; j < 6; ++j) { o.quad[6 * c + j] = Q[j]; o.aabb[6 * c + j] = bb[j]; }
+}
+
+__device__ void write_cell_f64(const MomOut &o, int64_t c, double M, const double com[3],
+                               const double Q[6], const float bb[6], bool has64) {
+    float ch[3], cl[3], q[6];
+    for (int a = 0; a < 3; ++a) {
+        ch[a] = __double2float_rn(com[a]);
+        cl[a] = __double2float_rn(__dsub_rn(com[a], (double)ch[a]));
+    }
+    for (int j = 0; j < 6; ++j) q[j] = __double2float_rn(Q[j]);
+    write_cell_f32(o, c, __double2float_rn(M), ch, cl, q, bb);
+    if (has64) {
+        o.mass64[c] = M;
+        for (int a = 0; a < 3; ++a) o.com64[3 * c + a] = com[a];
+        for (int j = 0; j < 6; ++j) o.quad64[6 * c + j] = Q[j];
+    }
+}
+
+// Leaf / chunk finalisation from raw sums about a reference point.
+__device__ void finish_c(const MomOut &o, int64_t c, const AccC &A, const float ref[3],
+                         const float bb[6]) {
+    float Mh, Ml;
+    fast_two_sum(A.M, A.Mc, Mh, Ml);
+    float rh[3], rl[3];
+    for (int a = 0; a < 3; ++a) {
+        float sh, sl;
+        fast_two_sum(A.S[a], A.Sc[a], sh, sl);
+        if (Mh != 0.f) df_div(sh, sl, Mh, Ml, rh[a], rl[a]);
+        else rh[a] = rl[a] = 0.f;
+    }
+    float Q[6];
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++j) {
+            // Q = S2 - M c c^T about the reference point
+            float t = __fmul_rn(Mh, rh[a]);
+            float p, pe;
+            two_prod(t, rh[b], p, pe);
+            float te = __fmaf_rn(Mh, rh[a], -t);
+            pe = __fmaf_rn(te, rh[b], pe);
+            pe = __fmaf_rn(Mh, __fmaf_rn(rh[a], rl[b], rl[a] * rh[b]), pe);
+            float qh, ql;
+            two_sum(A.Q[j], -p, qh, ql);
+            Q[j] = __fadd_rn(qh, __fadd_rn(ql, __fsub_rn(A.Qc[j], pe)));
+        }
+    float ch[3], cl[3];
+    for (int a = 0; a < 3; ++a) {
+        float h, l;
+        two_sum(ref[a], rh[a], h, l);
+        l = __fadd_rn(l, rl[a]);
+        fast_two_sum(h, l, ch[a], cl[a]);
+    }
+    write_cell_f32(o, c, Mh + Ml, ch, cl, Q, bb);
+}
+
+__device__ void finish_p(const MomOut &o, int64_t c, const AccP &A, const float ref[3],
+                         const float bb[6]) {
+    float r[3], ch[3], cl[3], Q[6];
+    for (int a = 0; a < 3; ++a) r[a] = (A.M != 0.f) ? A.S[a] / A.M : 0.f;
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++j) Q[j] = A.Q[j] - A.M * r[a] * r[b];
+    for (int a = 0; a < 3; ++a) { ch[a] = ref[a] + r[a]; cl[a] = 0.f; }
+    write_cell_f32(o, c, A.M, ch, cl, Q, bb);
+}
+
+__device__ void finish_d(const MomOut &o, int64_t c, const AccD &A, const float ref[3],
+                         const float bb[6], bool has64) {
+    double r[3], com[3], Q[6];
+    for (int a = 0; a < 3; ++a) r[a] = (A.M != 0.0) ? A.S[a] / A.M : 0.0;
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++j) Q[j] = A.Q[j] - A.M * r[a] * r[b];
+    for (int a = 0; a < 3; ++a) com[a] = (double)ref[a] + r[a];
+    write_cell_f64(o, c, A.M, com, Q, bb, has64);
+}
+
+// ------------------------------------------------------------- leaves
+
+__device__ __forceinline__ void load_particle(const float *__restrict__ pos,
+                                              const float *__restrict__ mass, float m_eq, int32_t i,
+                                              float x[3], float &m) {
+    x[0] = __ldg(pos + 3 * (int64_t)i);
+    x[1] = __ldg(pos + 3 * (int64_t)i + 1);
+    x[2] = __ldg(pos + 3 * (int64_t)i + 2);
+    m = mass ? __ldg(mass + i) : m_eq;
+}
+
+template <int MODE>
+__device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float *__restrict__ pos,
+                         const float *__restrict__ mass, float m_eq, int64_t c, int64_t pf,
+                         int64_t pe) {
+    float ref[3], bb[6], x[3], m;
+    const int32_t i0 = T.perm[pf];
+    load_particle(pos, mass, m_eq, i0, ref, m);
+    for (int a = 0; a < 3; ++a) { bb[a] = ref[a]; bb[3 + a] = ref[a]; }
+    const bool big = (pe - pf) > kBigCell;
+    if (MODE == TB_MOM_FP64 || big) {
+        AccD A;
+        A.init();
+        for (int64_t k = pf; k < pe; ++k) {
+            const int32_t i = (k == pf) ? i0 : T.perm[k];
+            load_particle(pos, mass, m_eq, i, x, m);
+            double dx[3];
+            for (int a = 0; a < 3; ++a) {
+                dx[a] = (double)x[a] - (double)ref[a];
+                bb[a] = fminf(bb[a], x[a]);
+                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            }
+            A.add((double)m, dx);
+            if (o.pos_sorted) {
+                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
+                o.mass_sorted[k] = m;
+            }
+        }
+        finish_d(o, c, A, ref, bb, MODE == TB_MOM_FP64);
+    } else if (MODE == TB_MOM_FP32_COMP) {
+        AccC A;
+        A.init();
+        for (int64_t k = pf; k < pe; ++k) {
+            const int32_t i = (k == pf) ? i0 : T.perm[k];
+            load_particle(pos, mass, m_eq, i, x, m);
+            float dx[3];
+            for (int a = 0; a < 3; ++a) {
+                dx[a] = __fsub_rn(x[a], ref[a]);
+                bb[a] = fminf(bb[a], x[a]);
+                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            }
+            A.add(m, dx);
+            if (o.pos_sorted) {
+                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
+                o.mass_sorted[k] = m;
+            }
+        }
+        finish_c(o, c, A, ref, bb);
+    } else {
+        AccP A;
+        A.init();
+        for (int64_t k = pf; k < pe; ++k) {
+            const int32_t i = (k == pf) ? i0 : T.perm[k];
+            load_particle(pos, mass, m_eq, i, x, m);
+            float dx[3];
+            for (int a = 0; a < 3; ++a) {
+                dx[a] = x[a] - ref[a];
+                bb[a] = fminf(bb[a], x[a]);
+                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            }
+            A.add(m, dx);
+            if (o.pos_sorted) {
+                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
+                o.mass_sorted[k] = m;
+            }
+        }
+        finish_p(o, c, A, ref, bb);
+    }
+}
+
+// ----------------------------------------------------------- parents
+
+template <int MODE>
+__device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
+    const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
+    float bb[6];
+    for (int a = 0; a < 3; ++a) { bb[a] = __ldcg(o.aabb + 6 * (int64_t)c0 + a); bb[3 + a] = __ldcg(o.aabb + 6 * (int64_t)c0 + 3 + a); }
+    for (int32_t c = c0 + 1; c < c1; ++c)
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(bb[a], __ldcg(o.aabb + 6 * (int64_t)c + a));
+            bb[3 + a] = fmaxf(bb[3 + a], __ldcg(o.aabb + 6 * (int64_t)c + 3 + a));
+        }
+    const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
+    if (MODE == TB_MOM_FP64 || big) {
+        double M = 0.0, S[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0}, cm[8][3], mc[8];
+        int nch = 0;
+        for (int32_t c = c0; c < c1; ++c, ++nch) {
+            double Mc, com[3];
+            if (MODE == TB_MOM_FP64) {
+                Mc = __ldcg(o.mass64 + c);
+                for (int a = 0; a < 3; ++a) com[a] = __ldcg(o.com64 + 3 * (int64_t)c + a);
+            } else {
+                Mc = (double)__ldcg(o.mass + c);
+                for (int a = 0; a < 3; ++a)
+                    com[a] = (double)__ldcg(o.com + 3 * (int64_t)c + a) +
+                             (double)__ldcg(o.com_lo + 3 * (int64_t)c + a);
+            }
+            mc[nch] = Mc;
+            for (int a = 0; a < 3; ++a) cm[nch][a] = com[a];
+            M += Mc;
+        }
+        // relative to the first child's centre
+        for (int j = 0; j < nch; ++j)
+            for (int a = 0; a < 3; ++a) S[a] += mc[j] * (cm[j][a] - cm[0][a]);
+        double r[3], com[3];
+        for (int a = 0; a < 3; ++a) {
+            r[a] = (M != 0.0) ? S[a] / M : 0.0;
+            com[a] = cm[0][a] + r[a];
+        }
+        for (int j = 0; j < nch; ++j) {
+            const int32_t c = c0 + j;
+            double e[3];
+            for (int a = 0; a < 3; ++a) e[a] = (cm[j][a] - cm[0][a]) - r[a];
+            int q = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a; b < 3; ++b, ++q) {
+                    double qc = (MODE == TB_MOM_FP64) ? __ldcg(o.quad64 + 6 * (int64_t)c + q)
+                                                      : (double)__ldcg(o.quad + 6 * (int64_t)c + q);
+                    Q[q] += qc + mc[j] * e[a] * e[b];
+                }
+        }
+        write_cell_f64(o, p, M, com, Q, bb, MODE == TB_MOM_FP64);
+    } else if (MODE == TB_MOM_FP32_COMP) {
+        float ref[3];
+        for (int a = 0; a < 3; ++a) ref[a] = __ldcg(o.com + 3 * (int64_t)c0 + a);
+        float Mh = 0.f, Mc = 0.f, Sh[3] = {0, 0, 0}, Sc[3] = {0, 0, 0};
+        float dh[8][3], dl[8][3], mm[8];
+        int nch = 0;
+        for (int32_t c = c0; c < c1; ++c, ++nch) {
+            float m = __ldcg(o.mass + c), e;
+            mm[nch] = m;
+            two_sum(Mh, m, Mh, e);
+            Mc += e;
+            for (int a = 0; a < 3; ++a) {
+                float h, l;
+                two_sum(__ldcg(o.com + 3 * (int64_t)c + a), -ref[a], h, l);
+                l = __fadd_rn(l, __ldcg(o.com_lo + 3 * (int64_t)c + a));
+                fast_two_sum(h, l, dh[nch][a], dl[nch][a]);
+                float pp, pe;
+                two_prod(m, dh[nch][a], pp, pe);
+                pe = __fmaf_rn(m, dl[nch][a], pe);
+                two_sum(Sh[a], pp, Sh[a], e);
+                Sc[a] += e + pe;
+            }
+        }
+        float MH, ML;
+        fast_two_sum(Mh, Mc, MH, ML);
+        float rh[3], rl[3];
+        for (int a = 0; a < 3; ++a) {
+            float sh, sl;
+            fast_two_sum(Sh[a], Sc[a], sh, sl);
+            if (MH != 0.f) df_div(sh, sl, MH, ML, rh[a], rl[a]);
+            else rh[a] = rl[a] = 0.f;
+        }
+        float Q[6], Qc[6];
+        for (int q = 0; q < 6; ++q) Q[q] = Qc[q] = 0.f;
+        for (int j = 0; j < nch; ++j) {
+            const int32_t c = c0 + j;
+            float e[3];
+            for (int a = 0; a < 3; ++a)
+                e[a] = __fadd_rn(__fsub_rn(dh[j][a], rh[a]), __fsub_rn(dl[j][a], rl[a]));
+            int q = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a; b < 3; ++b, ++q) {
+                    float s, er;
+                    two_sum(Q[q], __ldcg(o.quad + 6 * (int64_t)c + q), s, er);
+                    Q[q] = s;
+                    Qc[q] += er;
+                    float t, te, pp, pe;
+                    two_prod(mm[j], e[a], t, te);
+                    two_prod(t, e[b], pp, pe);
+                    pe = __fmaf_rn(te, e[b], pe);
+                    two_sum(Q[q], pp, s, er);
+                    Q[q] = s;
+                    Qc[q] += er + pe;
+                }
+        }
+        float Qf[6], ch[3], cl[3];
+        for (int q = 0; q < 6; ++q) Qf[q] = __fadd_rn(Q[q], Qc[q]);
+        for (int a = 0; a < 3; ++a) {
+            float h, l;
+            two_sum(ref[a], rh[a], h, l);
+            l = __fadd_rn(l, rl[a]);
+            fast_two_sum(h, l, ch[a], cl[a]);
+        }
+        write_cell_f32(o, p, MH + ML, ch, cl, Qf, bb);
+    } else {
+        float ref[3];
+        for (int a = 0; a < 3; ++a) ref[a] = __ldcg(o.com + 3 * (int64_t)c0 + a);
+        float M = 0.f, S[3] = {0, 0, 0};
+        for (int32_t c = c0; c < c1; ++c) {
+            float m = __ldcg(o.mass + c);
+            M += m;
+            for (int a = 0; a < 3; ++a) S[a] += m * (__ldcg(o.com + 3 * (int64_t)c + a) - ref[a]);
+        }
+        float r[3];
+        for (int a = 0; a < 3; ++a) r[a] = (M != 0.f) ? S[a] / M : 0.f;
+        float Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int32_t c = c0; c < c1; ++c) {
+            float m = __ldcg(o.mass + c), e[3];
+            for (int a = 0; a < 3; ++a) e[a] = (__ldcg(o.com + 3 * (int64_t)c + a) - ref[a]) - r[a];
+            int q = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a; b < 3; ++b, ++q) Q[q] += __ldcg(o.quad + 6 * (int64_t)c + q) + m * e[a] * e[b];
+        }
+        float ch[3], cl[3];
+        for (int a = 0; a < 3; ++a) { ch[a] = ref[a] + r[a]; cl[a] = 0.f; }
+        write_cell_f32(o, p, M, ch, cl, Q, bb);
+    }
+}
+
+// Climb from a finished cell while this thread brings the last child.
+template <int MODE>
+__device__ void climb(const TreeIn &T, const MomOut &o, int64_t c) {
+    __threadfence();
+    int64_t p = T.parent[c];
+    while (p >= 0) {
+        const uint32_t nch = (uint32_t)(T.child_end[p] - T.child_first[p]);
+        const uint32_t before = atomicAdd(&T.arrive[p], 1u);
+        if (before + 1 != nch) return;
+        __threadfence();
+        T.arrive[p] = 0;   // ready for the next moment call on this tree
+        combine_children<MODE>(T, o, p);
+        __threadfence();
+        p = T.parent[p];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kMomThreads)
+    leaf_moments_kernel(TreeIn T, MomOut o, const float *__restrict__ pos,
+                        const float *__restrict__ mass, float m_eq, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    const int64_t nl = info->n_leaves;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
+        const int64_t pf = T.leaf_pfirst[j];
+        const int64_t pe = (j + 1 < nl) ? T.leaf_pfirst[j + 1] : T.n;
+        const int64_t c = T.leaf_cell[j];
+        if (pe - pf > kBigLeafThread) {
+            uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
+            T.big_leaf[q] = (int32_t)j;
+            continue;
+        }
+        leaf_sum<MODE>(T, o, pos, mass, m_eq, c, pf, pe);
+        climb<MODE>(T, o, c);
+    }
+}
+
+// Block-wide sums of one long leaf, then the climb.
+template <int MODE>
+__global__ void __launch_bounds__(kBigThreads)
+    big_leaf_kernel(TreeIn T, MomOut o, const float *__restrict__ pos,
+                    const float *__restrict__ mass, float m_eq, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    __shared__ uint32_t s_q;
+    __shared__ float s_bb[kBigThreads][6];
+    __shared__ double s_d[kBigThreads][10];
+    __shared__ float s_f[kBigThreads][20];
+    const int64_t nl = info->n_leaves;
+    const uint32_t nq = *(volatile uint32_t *)&info->misc_ctr[2];
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(&info->misc_ctr[3], 1u);
+        __syncthreads();
+        const uint32_t q = s_q;
+        __syncthreads();
+        if (q >= nq) return;
+        const int64_t j = T.big_leaf[q];
+        const int64_t pf = T.leaf_pfirst[j];
+        const int64_t pe = (j + 1 < nl) ? T.leaf_pfirst[j + 1] : T.n;
+        const int64_t c = T.leaf_cell[j];
+        const int64_t cnt = pe - pf;
+        const int64_t chunk = (cnt + kBigThreads - 1) / kBigThreads;
+        const int64_t a0 = pf + threadIdx.x * chunk, a1 = min64(pe, a0 + chunk);
+        float ref[3], x[3], m, bb[6];
+        load_particle(pos, mass, m_eq, T.perm[pf], ref, m);
+        for (int a = 0; a < 3; ++a) { bb[a] = ref[a]; bb[3 + a] = ref[a]; }
+        const bool f64 = (MODE == TB_MOM_FP64) || cnt > kBigCell;
+        AccD D;
+        AccC Cc;
+        AccP Pp;
+        D.init(); Cc.init(); Pp.init();
+        for (int64_t k = a0; k < a1; ++k) {
+            load_particle(pos, mass, m_eq, T.perm[k], x, m);
+            for (int a = 0; a < 3; ++a) { bb[a] = fminf(bb[a], x[a]); bb[3 + a] = fmaxf(bb[3 + a], x[a]); }
+            if (o.pos_sorted) {
+                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
+                o.mass_sorted[k] = m;
+            }
+            if (f64) {
+                double dx[3];
+                for (int a = 0; a < 3; ++a) dx[a] = (double)x[a] - (double)ref[a];
+                D.add((double)m, dx);
+            } else {
+                float dx[3];
+                for (int a = 0; a < 3; ++a) dx[a] = __fsub_rn(x[a], ref[a]);
+                if (MODE == TB_MOM_FP32_COMP) Cc.add(m, dx);
+                else Pp.add(m, dx);
+            }
+        }
+        // tree reduction in shared memory, fixed order
+        for (int a = 0; a < 6; ++a) s_bb[threadIdx.x][a] = bb[a];
+        if (f64) {
+            s_d[threadIdx.x][0] = D.M;
+            for (int a = 0; a < 3; ++a) s_d[threadIdx.x][1 + a] = D.S[a];
+            for (int q2 = 0; q2 < 6; ++q2) s_d[threadIdx.x][4 + q2] = D.Q[q2];
+        } else if (MODE == TB_MOM_FP32_COMP) {
+            s_f[threadIdx.x][0] = Cc.M; s_f[threadIdx.x][1] = Cc.Mc;
+            for (int a = 0; a < 3; ++a) { s_f[threadIdx.x][2 + a] = Cc.S[a]; s_f[threadIdx.x][5 + a] = Cc.Sc[a]; }
+            for (int q2 = 0; q2 < 6; ++q2) { s_f[threadIdx.x][8 + q2] = Cc.Q[q2]; s_f[threadIdx.x][14 + q2] = Cc.Qc[q2]; }
+        } else {
+            s_f[threadIdx.x][0] = Pp.M;
+            for (int a = 0; a < 3; ++a) s_f[threadIdx.x][2 + a] = Pp.S[a];
+            for (int q2 = 0; q2 < 6; ++q2) s_f[threadIdx.x][8 + q2] = Pp.Q[q2];
+        }
+        __syncthreads();
+        for (int half = kBigThreads / 2; half > 0; half >>= 1) {
+            if (threadIdx.x < half) {
+                const int u = threadIdx.x, v = threadIdx.x + half;
+                for (int a = 0; a < 3; ++a) {
+                    s_bb[u][a] = fminf(s_bb[u][a], s_bb[v][a]);
+                    s_bb[u][3 + a] = fmaxf(s_bb[u][3 + a], s_bb[v][3 + a]);
+                }
+                if (f64) {
+                    for (int z = 0; z < 10; ++z) s_d[u][z] += s_d[v][z];
+                } else if (MODE == TB_MOM_FP32_COMP) {
+                    AccC A, B;
+                    A.M = s_f[u][0]; A.Mc = s_f[u][1]; B.M = s_f[v][0]; B.Mc = s_f[v][1];
+                    for (int a = 0; a < 3; ++a) {
+                        A.S[a] = s_f[u][2 + a]; A.Sc[a] = s_f[u][5 + a];
+                        B.S[a] = s_f[v][2 + a]; B.Sc[a] = s_f[v][5 + a];
+                    }
+                    for (int q2 = 0; q2 < 6; ++q2) {
+                        A.Q[q2] = s_f[u][8 + q2]; A.Qc[q2] = s_f[u][14 + q2];
+                        B.Q[q2] = s_f[v][8 + q2]; B.Qc[q2] = s_f[v][14 + q2];
+                    }
+                    A.merge(B);
+                    s_f[u][0] = A.M; s_f[u][1] = A.Mc;
+                    for (int a = 0; a < 3; ++a) { s_f[u][2 + a] = A.S[a]; s_f[u][5 + a] = A.Sc[a]; }
+                    for (int q2 = 0; q2 < 6; ++q2) { s_f[u][8 + q2] = A.Q[q2]; s_f[u][14 + q2] = A.Qc[q2]; }
+                } else {
+                    s_f[u][0] += s_f[v][0];
+                    for (int a = 0; a < 3; ++a) s_f[u][2 + a] += s_f[v][2 + a];
+                    for (int q2 = 0; q2 < 6; ++q2) s_f[u][8 + q2] += s_f[v][8 + q2];
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            float bbf[6];
+            for (int a = 0; a < 6; ++a) bbf[a] = s_bb[0][a];
+            if (f64) {
+                AccD A;
+                A.M = s_d[0][0];
+                for (int a = 0; a < 3; ++a) A.S[a] = s_d[0][1 + a];
+                for (int q2 = 0; q2 < 6; ++q2) A.Q[q2] = s_d[0][4 + q2];
+                finish_d(o, c, A, ref, bbf, MODE == TB_MOM_FP64);
+            } else if (MODE == TB_MOM_FP32_COMP) {
+                AccC A;
+                A.M = s_f[0][0]; A.Mc = s_f[0][1];
+                for (int a = 0; a < 3; ++a) { A.S[a] = s_f[0][2 + a]; A.Sc[a] = s_f[0][5 + a]; }
+                for (int q2 = 0; q2 < 6; ++q2) { A.Q[q2] = s_f[0][8 + q2]; A.Qc[q2] = s_f[0][14 + q2]; }
+                finish_c(o, c, A, ref, bbf);
+            } else {
+                AccP A;
+                A.M = s_f[0][0];
+                for (int a = 0; a < 3; ++a) A.S[a] = s_f[0][2 + a];
+                for (int q2 = 0; q2 < 6; ++q2) A.Q[q2] = s_f[0][8 + q2];
+                finish_p(o, c, A, ref, bbf);
+            }
+            climb<MODE>(T, o, c);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void wait_selftest_kernel(int64_t limit, uint32_t *status, const uint32_t *flag) {
+    int64_t iter = 0;
+    while (*(volatile const uint32_t *)flag == 0u) {
+        if (!poll_backoff(iter, limit)) {
+            flag_error(status, kErrTimeout);
+            return;
+        }
+    }
+}
+
+template <int MODE>
+cudaError_t moments_impl(tb_tree &t, const float *pos, const float *mass, Workspace &ws,
+                         cudaStream_t s) {
+    TreeIn T{t.perm, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
+             t.leaf_cell, ws.leaf_pfirst, ws.arrive, ws.big_leaf, t.n_particles};
+    MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64,
+             t.pos_sorted, t.mass_sorted};
+    const float m_eq = (float)(1.0 / (double)(t.n_particles > 0 ? t.n_particles : 1));
+    cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (t.n_particles / 4 + kMomThreads - 1) / kMomThreads;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, pos, mass, m_eq, ws.info);
+    ++g_launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, pos, mass, m_eq, ws.info);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_moments(tb_tree &t, const float *pos, const float *mass, Workspace &ws, int mode,
+                           cudaStream_t s) {
+    switch (mode) {
+        case TB_MOM_FP32_COMP: return moments_impl<TB_MOM_FP32_COMP>(t, pos, mass, ws, s);
+        case TB_MOM_FP32_PLAIN: return moments_impl<TB_MOM_FP32_PLAIN>(t, pos, mass, ws, s);
+        case TB_MOM_FP64: return moments_impl<TB_MOM_FP64>(t, pos, mass, ws, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_wait_selftest(int64_t limit, uint32_t *status, uint32_t *flag, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 1, 0, s>>>(limit, status, flag);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace tb

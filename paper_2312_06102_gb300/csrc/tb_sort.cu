@@ -1,0 +1,298 @@
+// tb_sort.cu -- stable LSD radix sort of (key, original index) pairs
+// (Sec. 2.3 step 2).
+//
+// The paper sorts on the CPU with parallel sorting by regular sampling; on
+// the GPU the keys are sorted by ceil(63 / b) stable least-significant-digit
+// passes of b bits (bit 63 is always 1).  Each pass is one "onesweep" launch
+// (Adinets & Merrill 2022):
+//   - every block takes the next tile id from an atomic counter, so a block
+//     only ever waits on tiles that blocks already running own;
+//   - it ranks its tile's digits stably, warp by warp (warp match + popc),
+//     in tile order;
+//   - it publishes its per-digit counts to a look-back array and walks back
+//     over earlier tiles until it meets an inclusive prefix (decoupled
+//     look-back); every wait is bounded and reports a timeout instead of
+//     hanging;
+//   - it orders the tile by digit in shared memory and writes keys and
+//     indices out as runs of consecutive addresses.
+// Digit offsets of every pass come from the histograms taken while the keys
+// were made.  Look-back words carry an epoch (build counter + pass) so that
+// the array is never cleared between passes or builds.
+#include "tb_device.cuh"
+
+namespace tb {
+
+namespace {
+
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagIncl = 2ull << 62;
+
+template <int RADIX_BITS, int THREADS, int ITEMS>
+struct SortSmem {
+    static constexpr int RADIX = 1 << RADIX_BITS;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int TILE = THREADS * ITEMS;
+    uint64_t keys[TILE];
+    int32_t vals[TILE];
+    uint32_t warp_hist[WARPS][RADIX + 1];
+    uint32_t tile_off[RADIX + 1];
+    uint32_t glob_base[RADIX];
+    uint32_t scan_tmp[WARPS];
+    uint32_t tile;
+};
+
+template <int RADIX_BITS, int THREADS, int ITEMS, bool FIRST>
+__global__ void __launch_bounds__(THREADS)
+    onesweep_kernel(const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
+                    uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
+                    int pass, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
+                    DevInfo *info, int64_t spin_limit) {
+    using S = SortSmem<RADIX_BITS, THREADS, ITEMS>;
+    constexpr int RADIX = S::RADIX;
+    constexpr int WARPS = S::WARPS;
+    constexpr int TILE = S::TILE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int shift = pass * RADIX_BITS;
+
+    if (threadIdx.x == 0) sm.tile = atomicAdd(&info->sort_tile_ctr[pass], 1u);
+    for (int i = threadIdx.x; i < WARPS * (RADIX + 1); i += THREADS)
+        (&sm.warp_hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = sm.tile;
+    const int64_t tile_base = (int64_t)tile * TILE;
+    const int valid = (int)min64(TILE, n - tile_base);
+
+    // load (warp-striped: warp w owns 32*ITEMS consecutive elements)
+    uint64_t key[ITEMS];
+    int32_t val[ITEMS];
+    uint32_t rank[ITEMS];
+    const int wbase = warp * 32 * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int e = wbase + i * 32 + lane;
+        if (e < valid) {
+            key[i] = keys_in[tile_base + e];
+            val[i] = FIRST ? (int32_t)(tile_base + e) : vals_in[tile_base + e];
+        } else {
+            key[i] = 0;
+            val[i] = 0;
+        }
+    }
+
+    // stable rank within the warp, in element order
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int e = wbase + i * 32 + lane;
+        uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader) {
+            before = sm.warp_hist[warp][d];
+            sm.warp_hist[warp][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[i] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per-digit: offsets of each warp within the digit, tile digit counts
+    uint32_t my_count[(RADIX + THREADS - 1) / THREADS];
+#pragma unroll
+    for (int r = 0; r < (RADIX + THREADS - 1) / THREADS; ++r) {
+        int d = r * THREADS + threadIdx.x;
+        uint32_t acc = 0;
+        if (d < RADIX) {
+            for (int w = 0; w < WARPS; ++w) {
+                uint32_t c = sm.warp_hist[w][d];
+                sm.warp_hist[w][d] = acc;
+                acc += c;
+            }
+        }
+        my_count[r] = acc;
+    }
+    // exclusive scan of the counts over digits (each thread holds a
+    // contiguous group of digits when RADIX > THREADS)
+    {
+        constexpr int PER = (RADIX + THREADS - 1) / THREADS;
+        // regroup: thread t owns digits [t*PER, t*PER+PER) for the scan
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            int d = r * THREADS + threadIdx.x;
+            if (d < RADIX) sm.tile_off[d] = my_count[r];
+        }
+        __syncthreads();
+        uint32_t loc[PER];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            int d = threadIdx.x * PER + r;
+            loc[r] = (d < RADIX) ? sm.tile_off[d] : 0u;
+            sum += loc[r];
+        }
+        uint32_t x = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) sm.scan_tmp[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += sm.scan_tmp[w];
+        uint32_t run = wpre + x - sum;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            int d = threadIdx.x * PER + r;
+            if (d < RADIX) sm.tile_off[d] = run;
+            run += loc[r];
+        }
+        if (threadIdx.x == 0) sm.tile_off[RADIX] = (uint32_t)valid;
+    }
+    __syncthreads();
+
+    // decoupled look-back, one digit per thread
+    const uint64_t epoch = (uint64_t)((info->epoch + (uint32_t)pass) & 0x3fffffffu);
+#pragma unroll
+    for (int r = 0; r < (RADIX + THREADS - 1) / THREADS; ++r) {
+        int d = r * THREADS + threadIdx.x;
+        if (d >= RADIX) continue;
+        uint32_t cnt = my_count[r];
+        uint64_t *slot = lookback + (int64_t)tile * RADIX + d;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st_relaxed_u64(slot, kFlagIncl | (epoch << 32) | cnt);
+        } else {
+            st_relaxed_u64(slot, kFlagAgg | (epoch << 32) | cnt);
+            int64_t pred = (int64_t)tile - 1;
+            int64_t iter = 0;
+            while (pred >= 0) {
+                uint64_t w = ld_relaxed_u64(lookback + pred * RADIX + d);
+                if (((w >> 32) & 0x3fffffffu) != epoch || (w >> 62) == 0) {
+                    if (!poll_backoff(iter, spin_limit)) {
+                        flag_error(&info->status, kErrTimeout);
+                        break;
+                    }
+                    continue;
+                }
+                excl += (uint32_t)w;
+                if ((w >> 62) == 2) break;
+                --pred;
+            }
+            st_relaxed_u64(slot, kFlagIncl | (epoch << 32) | (excl + cnt));
+        }
+        sm.glob_base[d] = digit_off[d] + excl - sm.tile_off[d];
+    }
+    __syncthreads();
+
+    // order the tile by digit in shared memory
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int e = wbase + i * 32 + lane;
+        if (e < valid) {
+            uint32_t d = (uint32_t)((key[i] >> shift) & (RADIX - 1));
+            uint32_t p = sm.tile_off[d] + sm.warp_hist[warp][d] + rank[i];
+            sm.keys[p] = key[i];
+            sm.vals[p] = val[i];
+        }
+    }
+    __syncthreads();
+
+    // write runs of equal digits to consecutive global addresses
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int j = i * THREADS + threadIdx.x;
+        if (j < valid) {
+            uint64_t k = sm.keys[j];
+            uint32_t d = (uint32_t)((k >> shift) & (RADIX - 1));
+            uint64_t dst = (uint64_t)sm.glob_base[d] + (uint32_t)j;
+            dst &= 0xffffffffull;
+            if ((int64_t)dst < n) {
+                keys_out[dst] = k;
+                vals_out[dst] = sm.vals[j];
+            } else {
+                flag_error(&info->status, kErrTimeout);
+            }
+        }
+    }
+}
+
+template <int B, int T, int I>
+cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int64_t n,
+                       Workspace &ws, uint64_t *&kout, int32_t *&pout, cudaStream_t s) {
+    using S = SortSmem<B, T, I>;
+    const int passes = sort_passes(B);
+    const size_t smem = sizeof(S);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(onesweep_kernel<B, T, I, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(onesweep_kernel<B, T, I, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const int64_t tiles = (n + S::TILE - 1) / S::TILE;
+    // the unsorted keys are in `ka`; passes alternate ka -> kb -> ka ...
+    uint64_t *src = ka, *dst = kb;
+    int32_t *vsrc = pa, *vdst = pb;
+    const int64_t spin = int64_t(1) << 26;
+    for (int p = 0; p < passes; ++p) {
+        if (p == 0)
+            onesweep_kernel<B, T, I, true><<<(unsigned)tiles, T, smem, s>>>(
+                src, nullptr, dst, vdst, n, p, ws.hist + p * (1 << B), ws.lookback, ws.info, spin);
+        else
+            onesweep_kernel<B, T, I, false><<<(unsigned)tiles, T, smem, s>>>(
+                src, vsrc, dst, vdst, n, p, ws.hist + p * (1 << B), ws.lookback, ws.info, spin);
+        ++g_launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mark(ws, "sort_pass", s);
+        uint64_t *t = src; src = dst; dst = t;
+        int32_t *u = vsrc; vsrc = vdst; vdst = u;
+    }
+    kout = src;
+    pout = vsrc;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+SortCfg default_sort_cfg(int radix_bits) {
+    switch (radix_bits) {
+        case 9: return {9, 256, 16};
+        case 10: return {10, 256, 16};
+        case 11: return {11, 256, 16};
+        default: return {8, 256, 16};
+    }
+}
+
+bool sort_cfg_valid(const SortCfg &c) {
+    return (c.radix_bits == 8 && c.threads == 256 && (c.items == 16 || c.items == 24)) ||
+           (c.radix_bits == 8 && c.threads == 512 && c.items == 12) ||
+           (c.radix_bits >= 9 && c.radix_bits <= 11 && c.threads == 256 && c.items == 16);
+}
+
+int64_t sort_tiles(const SortCfg &c, int64_t n) { return (n + c.tile() - 1) / c.tile(); }
+
+cudaError_t launch_sort(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int64_t n,
+                        Workspace &ws, const SortCfg &cfg, uint64_t *&kout, int32_t *&pout,
+                        cudaStream_t s) {
+    if (cfg.radix_bits == 8 && cfg.threads == 256 && cfg.items == 16)
+        return run_passes<8, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    if (cfg.radix_bits == 8 && cfg.threads == 256 && cfg.items == 24)
+        return run_passes<8, 256, 24>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    if (cfg.radix_bits == 8 && cfg.threads == 512 && cfg.items == 12)
+        return run_passes<8, 512, 12>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    if (cfg.radix_bits == 9) return run_passes<9, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    if (cfg.radix_bits == 10) return run_passes<10, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    if (cfg.radix_bits == 11) return run_passes<11, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tb

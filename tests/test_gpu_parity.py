@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Structure -- keys, permutation, cells, levels, links, ranges -- must be
+bit-exact; moments must meet the tolerances in gpu_util.  Sizes span several
+sort tiles (4096) and level tiles (4096) with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import clustered_halos, lattice, plummer, precision_stress, uniform_cube
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import (TOL_COM, TOL_MASS, TOL_QUAD, assert_structure_equal, gpu_tree,  # noqa: E402
+                      moment_errors, tb, to_np, torch)
+
+
+def _check(pos, mass, n_crit, mode=0, radix_bits=0, cell_capacity=0, tol_scale=1.0):
+    o = oracle.build_tree(pos, n_crit)
+    t, p, w = gpu_tree(pos, mass, n_crit, mode=mode, radix_bits=radix_bits,
+                       cell_capacity=cell_capacity)
+    assert_structure_equal(t, o)
+    M, com, quad, aabb = oracle.moments(o, pos, mass)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb, mode=mode)
+    assert bb_ok
+    assert em.max() <= TOL_MASS * tol_scale, em.max()
+    assert ec.max() <= TOL_COM * tol_scale, ec.max()
+    assert eq.max() <= TOL_QUAD * tol_scale, eq.max()
+    return t, o
+
+
+def test_uniform_65536():
+    """Plain single build, N = 65,536 uniform, n_crit = 16 (the small workload)."""
+    pos, mass = uniform_cube(65536, 1)
+    _check(pos, mass, 16)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 15, 16, 17, 33, 4095, 4096, 4097, 3 * 4096 + 77,
+                               50_001])
+def test_ragged_sizes(n):
+    pos, mass = uniform_cube(n, 1000 + n)
+    _check(pos, mass, 16)
+
+
+@pytest.mark.parametrize("radix_bits", [8, 9, 10, 11])
+def test_radix_widths(radix_bits):
+    pos, mass = plummer(70_000, 7)
+    _check(pos, mass, 8, radix_bits=radix_bits)
+
+
+@pytest.mark.parametrize("n_crit", [1, 2, 8, 32, 100, 1024])
+def test_n_crit_values(n_crit):
+    pos, mass = clustered_halos(60_000, 8, n_halo=200)
+    _check(pos, mass, n_crit)
+
+
+def test_plummer_deep():
+    pos, mass = plummer(1 << 18, 2)
+    t, o = _check(pos, mass, 16)
+    assert t.max_depth >= 8
+
+
+def test_clustered():
+    pos, mass = clustered_halos(1 << 18, 3, n_halo=500)
+    _check(pos, mass, 16)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_precision_stress_offset_box(mode):
+    """[1000,1001)^3 FP32 positions (many identical keys), log-normal masses."""
+    pos, mass = precision_stress(1 << 17, 5, n_halo=300)
+    t, o = _check(pos, mass, 16, mode=mode)
+    assert t.max_depth >= 10
+
+
+def test_null_mass_means_equal_masses():
+    pos, _ = uniform_cube(20_000, 4)
+    _check(pos, None, 16)
+
+
+def test_duplicates_and_identical():
+    rng = np.random.default_rng(3)
+    pos = rng.integers(0, 3, (30_000, 3)).astype(np.float32)
+    _check(pos, None, 4)
+    same = np.full((10_000, 3), 0.5, np.float32)
+    t, o = _check(same, None, 16)
+    assert t.n_cells == 22
+
+
+def test_lattice_complete_octree():
+    pos, mass = lattice(5)
+    t, o = _check(pos, mass, 1)
+    assert t.n_cells == sum(8 ** d for d in range(6))
+
+
+def test_fixed_capacity_and_rebuild_in_place():
+    m = tb()
+    pos, mass = uniform_cube(40_000, 9)
+    o = oracle.build_tree(pos, 16)
+    t, p, w = gpu_tree(pos, mass, 16, cell_capacity=o.n_cells + 10)
+    assert t.sync() == 0
+    assert_structure_equal(t, o)
+    # rebuild the same tree object with other particles
+    pos2, mass2 = plummer(30_000, 10)
+    o2 = oracle.build_tree(pos2, 16)
+    p2 = torch.from_numpy(pos2).cuda()
+    m.build(p2, None, n_crit=16, tree=t)
+    assert_structure_equal(t, o2)
+
+
+def test_capacity_overflow_reported():
+    m = tb()
+    pos, mass = uniform_cube(40_000, 9)
+    p = torch.from_numpy(pos).cuda()
+    t = m.build(p, None, n_crit=16, cell_capacity=100)
+    assert m.STATUS[t.sync()] == "TB_EOVERFLOW"
+    # the tree stays usable
+    m.build(p, None, n_crit=16, tree=t, cell_capacity=0)
+    assert t.sync() == 0
+
+
+def test_nonfinite_rejected():
+    m = tb()
+    pos, _ = uniform_cube(5000, 9)
+    pos[123, 1] = np.nan
+    with pytest.raises(m.TbError) as ei:
+        m.build(torch.from_numpy(pos).cuda(), None)
+    assert ei.value.name == "TB_ENONFINITE"
+    pos[123, 1] = np.inf
+    with pytest.raises(m.TbError):
+        m.build(torch.from_numpy(pos).cuda(), None)
+
+
+def test_argument_errors():
+    m = tb()
+    p = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
+    for kw in (dict(n_crit=0), dict(n_crit=2000), dict(mom_mode=7), dict(radix_bits=5)):
+        with pytest.raises(m.TbError) as ei:
+            m.build(p, None, **kw)
+        assert ei.value.name == "TB_EINVAL"
+
+
+def test_empty_input():
+    m = tb()
+    t = m.build(torch.zeros((0, 3), dtype=torch.float32, device="cuda"), None)
+    assert t.n_cells == 0
+    m.moments(t, torch.zeros((0, 3), dtype=torch.float32, device="cuda"))
+
+
+def test_plain_mode_structure_and_report():
+    """FP32-plain moments: same structure; errors reported, not bounded."""
+    pos, mass = plummer(1 << 16, 12)
+    o = oracle.build_tree(pos, 16)
+    t, p, w = gpu_tree(pos, mass, 16, mode=1)
+    assert_structure_equal(t, o)
+    M, com, quad, aabb = oracle.moments(o, pos, mass)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+    assert bb_ok and em.max() < 1e-4
+
+
+def test_reorder_output():
+    pos, mass = uniform_cube(30_000, 13)
+    o = oracle.build_tree(pos, 16)
+    t, p, w = gpu_tree(pos, mass, 16, reorder=True)
+    assert np.array_equal(to_np(t.pos_sorted), pos[o.perm])
+    assert np.array_equal(to_np(t.mass_sorted), mass[o.perm])
+
+
+def test_deterministic_repeat():
+    pos, mass = clustered_halos(1 << 17, 14, n_halo=300)
+    t1, p, w = gpu_tree(pos, mass, 16)
+    a = {k: to_np(getattr(t1, k)).copy() for k in ("mass", "com", "com_lo", "quad", "aabb")}
+    m = tb()
+    for _ in range(3):
+        m.build(p, w, n_crit=16, tree=t1)
+        m.moments(t1, p, w)
+        torch.cuda.synchronize()
+        for k, v in a.items():
+            assert np.array_equal(to_np(getattr(t1, k)), v), k
+
+
+def test_bounded_wait_times_out():
+    m = tb()
+    assert m.STATUS[m.selftest_wait(1000)] == "TB_ETIMEOUT"
+    # context still usable
+    pos, mass = uniform_cube(1000, 1)
+    _check(pos, mass, 16)
