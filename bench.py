@@ -60,7 +60,7 @@ def args_():
     ap.add_argument("--n", type=int, default=0, help="override particle count")
     ap.add_argument("--n-crit", type=int, default=0)
     ap.add_argument("--radix-bits", type=int, default=0)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 21)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -69,8 +69,8 @@ typedef struct {
     int32_t mom_mode;        /* tb_mom_mode */
     int64_t cell_capacity;   /* 0: size the cell arrays exactly (one stream sync);
                                 >0: fixed capacity, no host sync (graph-capturable) */
-    int32_t reorder;         /* 1: tb_moments also writes pos_sorted / mass_sorted
-                                (particles in key order, Sec. 2.3 step 3) */
+    int32_t reorder;         /* 1: tb_moments also writes pos_sorted (particles in key
+                                order, Sec. 2.3 step 3) */
     int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width) */
     int32_t batch_threads;   /* batched build: threads per set, 0 = tuned default */
     int32_t reserved;
@@ -114,8 +114,8 @@ typedef struct tb_tree {
     double *mass64;          /* FP64 mode only, else NULL */
     double *com64;
     double *quad64;
-    float *pos_sorted;       /* reorder only: [n][3] positions in key order, else NULL */
-    float *mass_sorted;      /* reorder only: [n] */
+    float *pos_sorted;       /* reorder only: [n][4] x, y, z, m in key order (Sec. 2.3
+                                step 3), written by tb_moments; else NULL */
 
     /* batched builds only (NULL / 0 otherwise) */
     int32_t n_sets;
@@ -144,9 +144,11 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
  * leaves by summation over their members in key order, every other cell
  * from its children (Sec. 2.3: properties are computed as cells are made,
  * the centre of mass of a parent from those of its children; higher
- * multipoles likewise).  d_pos / d_mass must be the arrays the tree was
- * built from.  Cells of more than 2^20 particles are summed in FP64 in
- * every mode. */
+ * multipoles likewise).  tb_build keeps a snapshot of (x, y, z, m) taken
+ * while it made the keys; when d_pos and d_mass are the same pointers the
+ * build was given, that snapshot is used, so their contents must not change
+ * in between.  Other pointers are read afresh.  Cells of more than 2^20
+ * particles are summed in FP64 in every mode. */
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
 
 /* Build S independent trees in one call, moments included.  Particles of set

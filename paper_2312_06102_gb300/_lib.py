@@ -42,7 +42,7 @@ class TreeC(C.Structure):
                 ("child_end", _vp), ("pfirst", _vp), ("pend", _vp), ("leaf_cell", _vp),
                 ("mass", _vp), ("com", _vp), ("com_lo", _vp), ("quad", _vp), ("aabb", _vp),
                 ("mass64", _vp), ("com64", _vp), ("quad64", _vp),
-                ("pos_sorted", _vp), ("mass_sorted", _vp),
+                ("pos_sorted", _vp),
                 ("n_sets", C.c_int32), ("set_particle_offset", _vp), ("set_cell_offset", _vp),
                 ("set_root", _vp), ("internal", _vp)]
 
@@ -183,8 +183,7 @@ class Tree:
     # particle arrays
     pkey = property(lambda s: _view(s.c.pkey, (s.n,), "u64"))
     perm = property(lambda s: _view(s.c.perm, (s.n,), "i32"))
-    pos_sorted = property(lambda s: _view(s.c.pos_sorted, (s.n, 3), "f32"))
-    mass_sorted = property(lambda s: _view(s.c.mass_sorted, (s.n,), "f32"))
+    pos_sorted = property(lambda s: _view(s.c.pos_sorted, (s.n, 4), "f32"))
     # cell arrays
     ckey = property(lambda s: _view(s.c.ckey, (s.n_cells,), "u64"))
     level = property(lambda s: _view(s.c.level, (s.n_cells,), "u8"))

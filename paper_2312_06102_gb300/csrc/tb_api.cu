@@ -83,9 +83,11 @@ void free_particles(TreeState &S) {
     tb_tree &t = S.pub;
     Workspace &ws = S.ws;
     dev_free(t.pkey); dev_free(t.perm); dev_free(ws.keys_alt); dev_free(ws.perm_alt);
+    dev_free(ws.xm);
+    ws.xm_pos = ws.xm_mass = nullptr;
     dev_free(t.leaf_cell); dev_free(ws.leaf_pfirst); dev_free(ws.big_leaf);
     dev_free(ws.level_cnt); dev_free(ws.lookback);
-    dev_free(t.pos_sorted); dev_free(t.mass_sorted);
+    dev_free(t.pos_sorted);
     ws.n_cap = 0;
     ws.tiles_cap = 0;
     ws.level_tiles_cap = 0;
@@ -118,7 +120,7 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         int64_t cap = n;
         int64_t lb = need_lb > 0 ? need_lb : 1;
         if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
-            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) ||
+            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) ||
             !dev_alloc(ws.leaf_pfirst, cap) || !dev_alloc(ws.big_leaf, cap) ||
             !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
             return TB_ENOMEM;
@@ -129,9 +131,7 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
     }
     if (reorder && (!t.pos_sorted || ws.n_cap > ws.reorder_cap)) {
         dev_free(t.pos_sorted);
-        dev_free(t.mass_sorted);
-        if (!dev_alloc(t.pos_sorted, 3 * ws.n_cap) || !dev_alloc(t.mass_sorted, ws.n_cap))
-            return TB_ENOMEM;
+        if (!dev_alloc(t.pos_sorted, 4 * ws.n_cap)) return TB_ENOMEM;
         ws.reorder_cap = ws.n_cap;
     }
     return TB_OK;
@@ -238,9 +238,9 @@ int64_t tb_kernel_launches(void) { return g_launches; }
 
 tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_params *params,
                    tb_stream stream, tb_tree **tree) {
-    (void)d_mass;
     if (!tree || !valid_params(params) || n < 0 || n > 2147483647LL) return TB_EINVAL;
     if (n > 0 && (!d_pos || (reinterpret_cast<uintptr_t>(d_pos) & 3u))) return TB_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_mass) & 3u) return TB_EINVAL;
     if (*tree && (*tree)->n_sets != 0) return TB_EINVAL;   // a batched tree
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TreeState *S = *tree ? state_of(*tree) : nullptr;
@@ -287,8 +287,10 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     uint64_t *kb = (passes & 1) ? t.pkey : ws.keys_alt;
     int32_t *pa = (passes & 1) ? ws.perm_alt : t.perm;
     int32_t *pb = (passes & 1) ? t.perm : ws.perm_alt;
-    e = launch_keys(d_pos, n, ka, ws, cfg, s);
+    e = launch_keys(d_pos, d_mass, n, ka, ws, cfg, s);
     if (e != cudaSuccess) return from_cuda(e);
+    ws.xm_pos = d_pos;
+    ws.xm_mass = d_mass;
     mark(ws, "keys", s);
     uint64_t *kout = nullptr;
     int32_t *pout = nullptr;
@@ -323,8 +325,16 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
         if (st != TB_OK) return st;
     }
     if (S->params.reorder && !tree->pos_sorted) return TB_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_mass) & 3u) return TB_EINVAL;
     S->ws.last_stream = s;
-    cudaError_t e = launch_moments(*tree, d_pos, d_mass, S->ws, S->params.mom_mode, s);
+    cudaError_t e = cudaSuccess;
+    if (d_pos != S->ws.xm_pos || d_mass != S->ws.xm_mass) {
+        e = launch_pack(d_pos, d_mass, tree->n_particles, S->ws.xm, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        S->ws.xm_pos = d_pos;
+        S->ws.xm_mass = d_mass;
+    }
+    e = launch_moments(*tree, d_pos, d_mass, S->ws, S->params.mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
     mark(S->ws, "moments", s);
     return TB_OK;

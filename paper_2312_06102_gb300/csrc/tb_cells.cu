@@ -105,10 +105,14 @@ __device__ void tile_levels(const uint64_t *__restrict__ skeys, int64_t n, int n
     __syncthreads();
     // L_i = max(c over [i-n, i]) = max(suffix max at i-n, prefix max at i)
     const int nL = (int)(e - s + 1);
-    for (int y = threadIdx.x; y < nL; y += blockDim.x) {
-        int x1 = y + ncrit;              // i - ext_lo for i = s - 1 + y
-        int x0 = y;                      // (i - n) - ext_lo
-        sm.L[y] = max(sm.sm[x0], sm.pm[x1]);
+    for (int y = threadIdx.x; y < kLvTile + 16; y += blockDim.x) {
+        if (y < nL) {
+            int x1 = y + ncrit;          // i - ext_lo for i = s - 1 + y
+            int x0 = y;                  // (i - n) - ext_lo
+            sm.L[y] = max(sm.sm[x0], sm.pm[x1]);
+        } else {
+            sm.L[y] = 0;                 // beyond the tile: with m = 255 starts nothing
+        }
     }
     const int nm = (int)(e - s);
     for (int y = threadIdx.x; y < kLvTile; y += blockDim.x) {

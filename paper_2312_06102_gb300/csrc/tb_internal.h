@@ -64,6 +64,9 @@ struct Workspace {
     int64_t cell_cap_request = 0;   // params.cell_capacity of the current build
     int64_t reorder_cap = 0;
 
+    float4 *xm = nullptr;            // [n] (x, y, z, m) in input order, written with the keys
+    const float *xm_pos = nullptr;   // arrays xm was made from
+    const float *xm_mass = nullptr;
     uint64_t *keys_alt = nullptr;
     int32_t *perm_alt = nullptr;
     uint32_t *hist = nullptr;        // [passes][radix]
@@ -103,8 +106,10 @@ struct Workspace {
 extern int64_t g_launches;
 
 cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len, cudaStream_t s);
-cudaError_t launch_keys(const float *pos, int64_t n, uint64_t *keys, Workspace &ws,
-                        const SortCfg &cfg, cudaStream_t s);
+cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
+                        Workspace &ws, const SortCfg &cfg, cudaStream_t s);
+cudaError_t launch_pack(const float *pos, const float *mass, int64_t n, float4 *xm,
+                        cudaStream_t s);
 cudaError_t launch_sort(uint64_t *keys_in_place_a, uint64_t *keys_b, int32_t *perm_a,
                         int32_t *perm_b, int64_t n, Workspace &ws, const SortCfg &cfg,
                         uint64_t *&keys_out, int32_t *&perm_out, cudaStream_t s);

@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
 }
 
 template <int RADIX_BITS>
-__global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restrict__ pos, int64_t n,
-                                                            bool vec, uint64_t *__restrict__ keys,
+__global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restrict__ pos,
+                                                            const float *__restrict__ mass,
+                                                            float m_eq, int64_t n, bool vec,
+                                                            uint64_t *__restrict__ keys,
+                                                            float4 *__restrict__ xm,
                                                             uint32_t *hist, int passes,
                                                             DevInfo *info) {
     constexpr int RADIX = 1 << RADIX_BITS;
@@ -184,21 +187,29 @@ __global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restr
         const float4 *p4 = reinterpret_cast<const float4 *>(pos);
         ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(keys);
         const int64_t groups = n / 4;
+        const float4 *m4 = reinterpret_cast<const float4 *>(mass);
         for (int64_t g = tid; g < groups; g += stride) {
             float4 a = __ldcs(p4 + 3 * g), c = __ldcs(p4 + 3 * g + 1), d = __ldcs(p4 + 3 * g + 2);
+            float4 w = mass ? __ldcs(m4 + g) : make_float4(m_eq, m_eq, m_eq, m_eq);
             uint64_t k0 = key_of(a.x, a.y, a.z);
             uint64_t k1 = key_of(a.w, c.x, c.y);
             uint64_t k2v = key_of(c.z, c.w, d.x);
             uint64_t k3 = key_of(d.y, d.z, d.w);
             k2[2 * g] = make_ulonglong2(k0, k1);
             k2[2 * g + 1] = make_ulonglong2(k2v, k3);
+            xm[4 * g] = make_float4(a.x, a.y, a.z, w.x);
+            xm[4 * g + 1] = make_float4(a.w, c.x, c.y, w.y);
+            xm[4 * g + 2] = make_float4(c.z, c.w, d.x, w.z);
+            xm[4 * g + 3] = make_float4(d.y, d.z, d.w, w.w);
             count(k0); count(k1); count(k2v); count(k3);
         }
         done = groups * 4;
     }
     for (int64_t i = done + tid; i < n; i += stride) {
-        uint64_t k = key_of(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
+        float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        uint64_t k = key_of(x, y, z);
         keys[i] = k;
+        xm[i] = make_float4(x, y, z, mass ? mass[i] : m_eq);
         count(k);
     }
     __syncthreads();
@@ -254,10 +265,12 @@ cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len
 }
 
 template <int B>
-static cudaError_t keys_impl(const float *pos, int64_t n, uint64_t *keys, Workspace &ws, int passes,
-                             cudaStream_t s) {
+static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uint64_t *keys,
+                             Workspace &ws, int passes, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(pos) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(mass) & 15u) == 0 &&
                      (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    const float m_eq = (float)(1.0 / (double)(n > 0 ? n : 1));
     size_t smem = sizeof(uint32_t) * passes * (1 << B);
     static bool attr = false;
     if (!attr) {
@@ -267,22 +280,42 @@ static cudaError_t keys_impl(const float *pos, int64_t n, uint64_t *keys, Worksp
     int64_t grid = 152 * 4;
     int64_t need = (n + 4 * kKeysThreads - 1) / (4 * kKeysThreads);
     if (need < grid) grid = need < 1 ? 1 : need;
-    keys_kernel<B><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, n, vec, keys, ws.hist, passes,
-                                                              ws.info);
+    keys_kernel<B><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, mass, m_eq, n, vec, keys, ws.xm,
+                                                              ws.hist, passes, ws.info);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_keys(const float *pos, int64_t n, uint64_t *keys, Workspace &ws,
-                        const SortCfg &cfg, cudaStream_t s) {
+cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
+                        Workspace &ws, const SortCfg &cfg, cudaStream_t s) {
     const int passes = sort_passes(cfg.radix_bits);
     switch (cfg.radix_bits) {
-        case 8: return keys_impl<8>(pos, n, keys, ws, passes, s);
-        case 9: return keys_impl<9>(pos, n, keys, ws, passes, s);
-        case 10: return keys_impl<10>(pos, n, keys, ws, passes, s);
-        case 11: return keys_impl<11>(pos, n, keys, ws, passes, s);
+        case 8: return keys_impl<8>(pos, mass, n, keys, ws, passes, s);
+        case 9: return keys_impl<9>(pos, mass, n, keys, ws, passes, s);
+        case 10: return keys_impl<10>(pos, mass, n, keys, ws, passes, s);
+        case 11: return keys_impl<11>(pos, mass, n, keys, ws, passes, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// (x, y, z, m) of each particle in input order, for moment calls whose
+// arrays differ from the ones the keys were made from.
+__global__ void pack_kernel(const float *__restrict__ pos, const float *__restrict__ mass,
+                            float m_eq, int64_t n, float4 *__restrict__ xm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        xm[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass ? mass[i] : m_eq);
+}
+
+cudaError_t launch_pack(const float *pos, const float *mass, int64_t n, float4 *xm,
+                        cudaStream_t s) {
+    const float m_eq = (float)(1.0 / (double)(n > 0 ? n : 1));
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    pack_kernel<<<(unsigned)grid, 256, 0, s>>>(pos, mass, m_eq, n, xm);
+    ++g_launches;
+    return cudaGetLastError();
 }
 
 int sort_passes(int radix_bits) { return (63 + radix_bits - 1) / radix_bits; }

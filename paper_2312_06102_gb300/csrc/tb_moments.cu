@@ -39,7 +39,7 @@ constexpr int kBigThreads = 256;
 struct MomOut {
     float *mass, *com, *com_lo, *quad, *aabb;
     double *mass64, *com64, *quad64;
-    float *pos_sorted, *mass_sorted;
+    float *pos_sorted;   // [n][4] x y z m in key order, or NULL
 };
 
 struct TreeIn {
@@ -236,82 +236,58 @@ __device__ void finish_d(const MomOut &o, int64_t c, const AccD &A, const float 
 
 // ------------------------------------------------------------- leaves
 
-__device__ __forceinline__ void load_particle(const float *__restrict__ pos,
-                                              const float *__restrict__ mass, float m_eq, int32_t i,
-                                              float x[3], float &m) {
-    x[0] = __ldg(pos + 3 * (int64_t)i);
-    x[1] = __ldg(pos + 3 * (int64_t)i + 1);
-    x[2] = __ldg(pos + 3 * (int64_t)i + 2);
-    m = mass ? __ldg(mass + i) : m_eq;
-}
-
+// Sum the members [pf, pe) of one leaf.  Member indices come from the
+// permutation; the (x, y, z, m) records are gathered eight at a time, all
+// eight loads issued before any is used, so each thread keeps several
+// independent memory requests in flight.
 template <int MODE>
-__device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float *__restrict__ pos,
-                         const float *__restrict__ mass, float m_eq, int64_t c, int64_t pf,
-                         int64_t pe) {
-    float ref[3], bb[6], x[3], m;
-    const int32_t i0 = T.perm[pf];
-    load_particle(pos, mass, m_eq, i0, ref, m);
-    for (int a = 0; a < 3; ++a) { bb[a] = ref[a]; bb[3 + a] = ref[a]; }
-    const bool big = (pe - pf) > kBigCell;
-    if (MODE == TB_MOM_FP64 || big) {
-        AccD A;
-        A.init();
-        for (int64_t k = pf; k < pe; ++k) {
-            const int32_t i = (k == pf) ? i0 : T.perm[k];
-            load_particle(pos, mass, m_eq, i, x, m);
-            double dx[3];
+__device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float4 *__restrict__ xm,
+                         int64_t c, int64_t pf, int64_t pe) {
+    constexpr int G = 8;
+    const float4 r0 = __ldg(xm + T.perm[pf]);
+    const float ref[3] = {r0.x, r0.y, r0.z};
+    float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+    const bool f64 = MODE == TB_MOM_FP64 || (pe - pf) > kBigCell;
+    AccD D;
+    AccC A;
+    AccP P;
+    D.init(); A.init(); P.init();
+    float4 *srt = reinterpret_cast<float4 *>(o.pos_sorted);
+    for (int64_t k0 = pf; k0 < pe; k0 += G) {
+        const int cnt = (int)min64(G, pe - k0);
+        int32_t idx[G];
+        float4 v[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) idx[j] = (j < cnt) ? __ldg(T.perm + k0 + j) : 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (j < cnt) v[j] = __ldg(xm + idx[j]);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (j >= cnt) break;
+            const float x[3] = {v[j].x, v[j].y, v[j].z};
             for (int a = 0; a < 3; ++a) {
-                dx[a] = (double)x[a] - (double)ref[a];
                 bb[a] = fminf(bb[a], x[a]);
                 bb[3 + a] = fmaxf(bb[3 + a], x[a]);
             }
-            A.add((double)m, dx);
-            if (o.pos_sorted) {
-                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
-                o.mass_sorted[k] = m;
+            if (f64) {
+                const double dx[3] = {(double)x[0] - (double)ref[0], (double)x[1] - (double)ref[1],
+                                      (double)x[2] - (double)ref[2]};
+                D.add((double)v[j].w, dx);
+            } else if (MODE == TB_MOM_FP32_COMP) {
+                const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
+                                     __fsub_rn(x[2], ref[2])};
+                A.add(v[j].w, dx);
+            } else {
+                const float dx[3] = {x[0] - ref[0], x[1] - ref[1], x[2] - ref[2]};
+                P.add(v[j].w, dx);
             }
+            if (srt) srt[k0 + j] = v[j];
         }
-        finish_d(o, c, A, ref, bb, MODE == TB_MOM_FP64);
-    } else if (MODE == TB_MOM_FP32_COMP) {
-        AccC A;
-        A.init();
-        for (int64_t k = pf; k < pe; ++k) {
-            const int32_t i = (k == pf) ? i0 : T.perm[k];
-            load_particle(pos, mass, m_eq, i, x, m);
-            float dx[3];
-            for (int a = 0; a < 3; ++a) {
-                dx[a] = __fsub_rn(x[a], ref[a]);
-                bb[a] = fminf(bb[a], x[a]);
-                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
-            }
-            A.add(m, dx);
-            if (o.pos_sorted) {
-                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
-                o.mass_sorted[k] = m;
-            }
-        }
-        finish_c(o, c, A, ref, bb);
-    } else {
-        AccP A;
-        A.init();
-        for (int64_t k = pf; k < pe; ++k) {
-            const int32_t i = (k == pf) ? i0 : T.perm[k];
-            load_particle(pos, mass, m_eq, i, x, m);
-            float dx[3];
-            for (int a = 0; a < 3; ++a) {
-                dx[a] = x[a] - ref[a];
-                bb[a] = fminf(bb[a], x[a]);
-                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
-            }
-            A.add(m, dx);
-            if (o.pos_sorted) {
-                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
-                o.mass_sorted[k] = m;
-            }
-        }
-        finish_p(o, c, A, ref, bb);
     }
+    if (f64) finish_d(o, c, D, ref, bb, MODE == TB_MOM_FP64);
+    else if (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
+    else finish_p(o, c, P, ref, bb);
 }
 
 // ----------------------------------------------------------- parents
@@ -474,8 +450,7 @@ __device__ void climb(const TreeIn &T, const MomOut &o, int64_t c) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads)
-    leaf_moments_kernel(TreeIn T, MomOut o, const float *__restrict__ pos,
-                        const float *__restrict__ mass, float m_eq, DevInfo *info) {
+    leaf_moments_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xm, DevInfo *info) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     const int64_t nl = info->n_leaves;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -488,7 +463,7 @@ __global__ void __launch_bounds__(kMomThreads)
             T.big_leaf[q] = (int32_t)j;
             continue;
         }
-        leaf_sum<MODE>(T, o, pos, mass, m_eq, c, pf, pe);
+        leaf_sum<MODE>(T, o, xm, c, pf, pe);
         climb<MODE>(T, o, c);
     }
 }
@@ -496,8 +471,7 @@ __global__ void __launch_bounds__(kMomThreads)
 // Block-wide sums of one long leaf, then the climb.
 template <int MODE>
 __global__ void __launch_bounds__(kBigThreads)
-    big_leaf_kernel(TreeIn T, MomOut o, const float *__restrict__ pos,
-                    const float *__restrict__ mass, float m_eq, DevInfo *info) {
+    big_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xm, DevInfo *info) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     __shared__ uint32_t s_q;
     __shared__ float s_bb[kBigThreads][6];
@@ -519,7 +493,10 @@ __global__ void __launch_bounds__(kBigThreads)
         const int64_t chunk = (cnt + kBigThreads - 1) / kBigThreads;
         const int64_t a0 = pf + threadIdx.x * chunk, a1 = min64(pe, a0 + chunk);
         float ref[3], x[3], m, bb[6];
-        load_particle(pos, mass, m_eq, T.perm[pf], ref, m);
+        {
+            const float4 r0 = __ldg(xm + T.perm[pf]);
+            ref[0] = r0.x; ref[1] = r0.y; ref[2] = r0.z;
+        }
         for (int a = 0; a < 3; ++a) { bb[a] = ref[a]; bb[3 + a] = ref[a]; }
         const bool f64 = (MODE == TB_MOM_FP64) || cnt > kBigCell;
         AccD D;
@@ -527,12 +504,10 @@ __global__ void __launch_bounds__(kBigThreads)
         AccP Pp;
         D.init(); Cc.init(); Pp.init();
         for (int64_t k = a0; k < a1; ++k) {
-            load_particle(pos, mass, m_eq, T.perm[k], x, m);
+            const float4 v = __ldg(xm + T.perm[k]);
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; m = v.w;
             for (int a = 0; a < 3; ++a) { bb[a] = fminf(bb[a], x[a]); bb[3 + a] = fmaxf(bb[3 + a], x[a]); }
-            if (o.pos_sorted) {
-                for (int a = 0; a < 3; ++a) o.pos_sorted[3 * k + a] = x[a];
-                o.mass_sorted[k] = m;
-            }
+            if (o.pos_sorted) reinterpret_cast<float4 *>(o.pos_sorted)[k] = v;
             if (f64) {
                 double dx[3];
                 for (int a = 0; a < 3; ++a) dx[a] = (double)x[a] - (double)ref[a];
@@ -636,18 +611,17 @@ cudaError_t moments_impl(tb_tree &t, const float *pos, const float *mass, Worksp
     TreeIn T{t.perm, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
              t.leaf_cell, ws.leaf_pfirst, ws.arrive, ws.big_leaf, t.n_particles};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64,
-             t.pos_sorted, t.mass_sorted};
-    const float m_eq = (float)(1.0 / (double)(t.n_particles > 0 ? t.n_particles : 1));
+             t.pos_sorted};
     cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int64_t grid = (t.n_particles / 4 + kMomThreads - 1) / kMomThreads;
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
-    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, pos, mass, m_eq, ws.info);
+    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xm, ws.info);
     ++g_launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, pos, mass, m_eq, ws.info);
+    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xm, ws.info);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -163,8 +163,24 @@ def test_reorder_output():
     pos, mass = uniform_cube(30_000, 13)
     o = oracle.build_tree(pos, 16)
     t, p, w = gpu_tree(pos, mass, 16, reorder=True)
-    assert np.array_equal(to_np(t.pos_sorted), pos[o.perm])
-    assert np.array_equal(to_np(t.mass_sorted), mass[o.perm])
+    xs = to_np(t.pos_sorted)
+    assert np.array_equal(xs[:, :3], pos[o.perm])
+    assert np.array_equal(xs[:, 3], mass[o.perm])
+
+
+def test_moments_with_other_arrays_than_the_build():
+    """New masses through other pointers are read afresh (no stale snapshot)."""
+    m = tb()
+    pos, mass = plummer(30_000, 15)
+    o = oracle.build_tree(pos, 16)
+    t, p, w = gpu_tree(pos, mass, 16)
+    mass2 = (mass * np.float32(3.0)).astype(np.float32)
+    w2 = torch.from_numpy(mass2).cuda()
+    m.moments(t, p, w2)
+    torch.cuda.synchronize()
+    M, com, quad, aabb = oracle.moments(o, pos, mass2)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+    assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
 
 
 def test_deterministic_repeat():
