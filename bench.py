@@ -60,6 +60,7 @@ def args_():
     ap.add_argument("--n", type=int, default=0, help="override particle count")
     ap.add_argument("--n-crit", type=int, default=0)
     ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -80,7 +81,7 @@ def peaks():
 
 def kernel_digest():
     h = hashlib.sha256()
-    for f in ("tb_sort.cu", "tb_device.cuh"):
+    for f in ("tb_sort.cu", "tb_device.cuh", "tb_internal.h"):
         with open(os.path.join(ROOT, "paper_2312_06102_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -219,14 +220,23 @@ def run_ours(a):
     w = hmass.cuda()
     stream = torch.cuda.current_stream()
 
+    # pick the radix-sort variant on this workload (untimed), unless one is named
+    cfg = None
+    tune_ms = None
+    if a.radix_bits:
+        cfg = next(v for v in tb.sort_variants() if v[0] == a.radix_bits)
+    elif not a.no_autotune:
+        from paper_2312_06102_gb300 import autotune
+        cfg, tune_ms = autotune.tune(p, w, n_crit=n_crit)
+        log(f"[bench] autotune: {cfg} " + " ".join(f"{k}:{v:.3f}" for k, v in tune_ms.items()))
     # first build sizes the cell arrays; later builds use that capacity and
     # need no host synchronisation
-    tree = tb.build(p, w, n_crit=n_crit, radix_bits=a.radix_bits)
+    tree = tb.build(p, w, n_crit=n_crit, sort_cfg=cfg)
     C = tree.n_cells
     tb.moments(tree, p, w)
     torch.cuda.synchronize()
     for _ in range(a.warmup):
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
         tb.moments(tree, p, w)
     torch.cuda.synchronize()
     st = tree.sync()
@@ -244,7 +254,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
         tb.moments(tree, p, w)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -297,7 +307,9 @@ def run_ours(a):
            "vs_baseline": None, "dtype": "f32+u64",
            "data": "synthetic (seeded generator, same draw on every rank)",
            "config": {"workload": a.workload, "n_particles": n, "n_crit": n_crit,
-                      "n_cells": C, "radix_bits": a.radix_bits or 8,
+                      "n_cells": C, "sort_variant": list(cfg) if cfg else "library default",
+                      "autotune_ms": ({",".join(map(str, k)): round(v, 3) for k, v in tune_ms.items()}
+                                      if tune_ms else None),
                       "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (1.6 GB positions vs 129 MB), no flush",
                       "mom_mode": "fp32_compensated"},
@@ -312,7 +324,7 @@ def run_ours(a):
     # end to end through the C ABI from pinned host buffers
     if not a.no_e2e:
         res = torch.empty(10, dtype=torch.float32).pin_memory()
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
         torch.cuda.synchronize()
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -321,7 +333,7 @@ def run_ours(a):
         for _ in range(a.steps):
             p.copy_(hpos, non_blocking=True)
             w.copy_(hmass, non_blocking=True)
-            tb.build(p, w, n_crit=n_crit, cell_capacity=C, radix_bits=a.radix_bits, tree=tree)
+            tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
             tb.moments(tree, p, w)
             root = torch.cat([tree.mass[:1], tree.com[0], tree.quad[0]])
             res.copy_(root, non_blocking=True)

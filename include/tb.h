@@ -72,6 +72,9 @@ typedef struct {
     int32_t reorder;         /* 1: tb_moments also writes pos_sorted (particles in key
                                 order, Sec. 2.3 step 3) */
     int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width) */
+    int32_t sort_threads;    /* 0 = tuned default; else threads per sort tile */
+    int32_t sort_items;      /* 0 = tuned default; else keys per thread of a sort tile
+                                (compiled variants: see tb_sort_variant) */
     int32_t batch_threads;   /* batched build: threads per set, 0 = tuned default */
     int32_t reserved;
 } tb_params;
@@ -176,6 +179,11 @@ const char *tb_status_string(tb_status s);
 
 /* Default parameters: n_crit 16, compensated FP32 moments, exact sizing. */
 tb_params tb_default_params(void);
+
+/* The i-th compiled radix-sort variant (digit bits, threads, keys per
+ * thread); returns 0 past the last one.  Any of them may be named in
+ * tb_params; the autotuner times them. */
+int32_t tb_sort_variant(int32_t i, int32_t *radix_bits, int32_t *threads, int32_t *items);
 
 /* Number of kernels this library has launched in this process so far. */
 int64_t tb_kernel_launches(void);

@@ -27,5 +27,6 @@ from ._lib import (  # noqa: F401
     library_path,
     moments,
     selftest_wait,
+    sort_variants,
     status_string,
 )

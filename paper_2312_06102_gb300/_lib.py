@@ -25,8 +25,8 @@ class TbError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("n_crit", C.c_int32), ("mom_mode", C.c_int32), ("cell_capacity", C.c_int64),
-                ("reorder", C.c_int32), ("radix_bits", C.c_int32), ("batch_threads", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reorder", C.c_int32), ("radix_bits", C.c_int32), ("sort_threads", C.c_int32),
+                ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("reserved", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -84,6 +84,8 @@ def lib():
         L.tb_stage_times.restype = C.c_int32
         L.tb_stage_name.argtypes = [P(TreeC), C.c_int32]
         L.tb_stage_name.restype = C.c_char_p
+        L.tb_sort_variant.argtypes = [C.c_int32, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+        L.tb_sort_variant.restype = C.c_int32
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
         L.tb_selftest_wait.restype = C.c_int
         _lib = L
@@ -206,7 +208,17 @@ class Tree:
     set_root = property(lambda s: _view(s.c.set_root, (s.n_sets, 4), "f64"))
 
 
-def _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, batch_threads):
+def sort_variants():
+    """(radix_bits, threads, items) of every compiled radix-sort variant."""
+    out, i = [], 0
+    b, t, k = C.c_int32(), C.c_int32(), C.c_int32()
+    while lib().tb_sort_variant(i, C.byref(b), C.byref(t), C.byref(k)):
+        out.append((b.value, t.value, k.value))
+        i += 1
+    return out
+
+
+def _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, batch_threads, sort_cfg=None):
     p = lib().tb_default_params()
     p.n_crit = int(n_crit)
     p.mom_mode = int(mom_mode)
@@ -214,6 +226,8 @@ def _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, batch_threads)
     p.reorder = int(reorder)
     p.radix_bits = int(radix_bits)
     p.batch_threads = int(batch_threads)
+    if sort_cfg:
+        p.radix_bits, p.sort_threads, p.sort_items = (int(v) for v in sort_cfg)
     return p
 
 
@@ -224,12 +238,16 @@ def _check(code, what):
 
 def build(pos: torch.Tensor, mass: torch.Tensor | None = None, n_crit: int = 16,
           mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0, reorder: bool = False,
-          radix_bits: int = 0, tree: Tree | None = None, stream=None) -> Tree:
-    """tb_build on a [n,3] float32 CUDA tensor; returns (or rebuilds) a Tree."""
+          radix_bits: int = 0, tree: Tree | None = None, stream=None, sort_cfg=None) -> Tree:
+    """tb_build on a [n,3] float32 CUDA tensor; returns (or rebuilds) a Tree.
+    sort_cfg = (radix_bits, threads, items) picks a compiled sort variant."""
     if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3:
         raise ValueError("pos must be a [n,3] float32 tensor")
     t = tree if tree is not None else Tree()
-    p = _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, 0)
+    if sort_cfg is None and not radix_bits:
+        from . import autotune
+        sort_cfg = autotune.cached(pos.shape[0])
+    p = _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, 0, sort_cfg)
     code = lib().tb_build(_ptr(pos), _ptr(mass), pos.shape[0], C.byref(p), _stream(stream),
                           C.byref(t._p))
     _check(code, "tb_build")

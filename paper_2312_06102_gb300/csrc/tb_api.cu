@@ -74,7 +74,6 @@ void free_cells(TreeState &S) {
     dev_free(t.child_end); dev_free(t.pfirst); dev_free(t.pend);
     dev_free(t.mass); dev_free(t.com); dev_free(t.com_lo); dev_free(t.quad); dev_free(t.aabb);
     dev_free(t.mass64); dev_free(t.com64); dev_free(t.quad64);
-    dev_free(S.ws.arrive);
     t.cell_capacity = 0;
     S.ws.cell_cap = 0;
 }
@@ -84,10 +83,11 @@ void free_particles(TreeState &S) {
     Workspace &ws = S.ws;
     dev_free(t.pkey); dev_free(t.perm); dev_free(ws.keys_alt); dev_free(ws.perm_alt);
     dev_free(ws.xm);
+    dev_free(ws.xs);
+    t.pos_sorted = nullptr;
     ws.xm_pos = ws.xm_mass = nullptr;
-    dev_free(t.leaf_cell); dev_free(ws.leaf_pfirst); dev_free(ws.big_leaf);
+    dev_free(t.leaf_cell); dev_free(ws.big_leaf);
     dev_free(ws.level_cnt); dev_free(ws.lookback);
-    dev_free(t.pos_sorted);
     ws.n_cap = 0;
     ws.tiles_cap = 0;
     ws.level_tiles_cap = 0;
@@ -120,8 +120,8 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         int64_t cap = n;
         int64_t lb = need_lb > 0 ? need_lb : 1;
         if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
-            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) ||
-            !dev_alloc(ws.leaf_pfirst, cap) || !dev_alloc(ws.big_leaf, cap) ||
+            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) || !dev_alloc(ws.xs, cap) ||
+            !dev_alloc(ws.big_leaf, cap) ||
             !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
             return TB_ENOMEM;
         if (cudaMemset(ws.lookback, 0, sizeof(uint64_t) * lb) != cudaSuccess) return TB_ECUDA;
@@ -129,11 +129,9 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         ws.tiles_cap = lb;
         ws.level_tiles_cap = ltiles;
     }
-    if (reorder && (!t.pos_sorted || ws.n_cap > ws.reorder_cap)) {
-        dev_free(t.pos_sorted);
-        if (!dev_alloc(t.pos_sorted, 4 * ws.n_cap)) return TB_ENOMEM;
-        ws.reorder_cap = ws.n_cap;
-    }
+    // the key-ordered records the moments are summed from are the reorder
+    // output of Sec. 2.3 step 3; they are exposed when asked for
+    t.pos_sorted = reorder ? reinterpret_cast<float *>(ws.xs) : nullptr;
     return TB_OK;
 }
 
@@ -148,8 +146,7 @@ tb_status ensure_cells(TreeState &S, int64_t cells, bool fp64) {
             !dev_alloc(t.child_first, cap) || !dev_alloc(t.child_end, cap) ||
             !dev_alloc(t.pfirst, cap) || !dev_alloc(t.pend, cap) || !dev_alloc(t.mass, cap) ||
             !dev_alloc(t.com, 3 * cap) || !dev_alloc(t.com_lo, 3 * cap) ||
-            !dev_alloc(t.quad, 6 * cap) || !dev_alloc(t.aabb, 6 * cap) ||
-            !dev_alloc(ws.arrive, cap))
+            !dev_alloc(t.quad, 6 * cap) || !dev_alloc(t.aabb, 6 * cap))
             return TB_ENOMEM;
         if (fp64 && (!dev_alloc(t.mass64, cap) || !dev_alloc(t.com64, 3 * cap) ||
                      !dev_alloc(t.quad64, 6 * cap)))
@@ -181,15 +178,18 @@ tb_status read_info(TreeState &S, cudaStream_t s) {
     return from_dev(S.ws.h_info->status);
 }
 
+SortCfg pick_cfg(const tb_params *p) {
+    SortCfg c = default_sort_cfg(p->radix_bits ? p->radix_bits : 8);
+    if (p->sort_threads) c.threads = p->sort_threads;
+    if (p->sort_items) c.items = p->sort_items;
+    return c;
+}
+
 bool valid_params(const tb_params *p) {
     return p && p->n_crit >= 1 && p->n_crit <= kMaxNcrit && p->mom_mode >= 0 && p->mom_mode <= 2 &&
            p->cell_capacity >= 0 &&
-           (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11));
-}
-
-SortCfg pick_cfg(const tb_params *p) {
-    if (p->radix_bits) return default_sort_cfg(p->radix_bits);
-    return default_sort_cfg(8);
+           (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11)) &&
+           sort_cfg_valid(pick_cfg(p));
 }
 
 }  // namespace
@@ -235,6 +235,15 @@ const char *tb_status_string(tb_status s) {
 }
 
 int64_t tb_kernel_launches(void) { return g_launches; }
+
+int32_t tb_sort_variant(int32_t i, int32_t *radix_bits, int32_t *threads, int32_t *items) {
+    const SortCfg *c = sort_variant(i);
+    if (!c) return 0;
+    if (radix_bits) *radix_bits = c->radix_bits;
+    if (threads) *threads = c->threads;
+    if (items) *items = c->items;
+    return 1;
+}
 
 tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_params *params,
                    tb_stream stream, tb_tree **tree) {
@@ -334,9 +343,8 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
         S->ws.xm_pos = d_pos;
         S->ws.xm_mass = d_mass;
     }
-    e = launch_moments(*tree, d_pos, d_mass, S->ws, S->params.mom_mode, s);
+    e = launch_moments(*tree, S->ws, S->params.mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
-    mark(S->ws, "moments", s);
     return TB_OK;
 }
 

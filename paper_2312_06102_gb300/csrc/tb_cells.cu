@@ -254,8 +254,7 @@ struct EmitOut {
     uint64_t *ckey;
     uint8_t *level;
     int32_t *parent, *child_first, *child_end, *pfirst, *pend;
-    int32_t *leaf_cell, *leaf_pfirst;
-    uint32_t *arrive;
+    int32_t *leaf_cell;
 };
 
 __global__ void __launch_bounds__(kLvThreads)
@@ -329,12 +328,10 @@ __global__ void __launch_bounds__(kLvThreads)
                 out.pfirst[idx] = (int32_t)k;
                 out.parent[idx] = (d == 0) ? -1 : (int32_t)s_P[d - 1][threadIdx.x] - 1;
                 out.child_first[idx] = (d < L) ? (int32_t)s_P[d + 1][threadIdx.x] : -1;
-                out.arrive[idx] = 0;
                 s_P[d][threadIdx.x] = (uint32_t)idx + 1;
             }
             uint32_t leaf = s_P[kLevels][threadIdx.x];
             out.leaf_cell[leaf] = (int32_t)s_P[L][threadIdx.x] - 1;
-            out.leaf_pfirst[leaf] = (int32_t)k;
             s_P[kLevels][threadIdx.x] = leaf + 1;
         }
         if (k == n - 1) {
@@ -379,7 +376,7 @@ cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int ncrit, Workspace &
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
     const size_t smem = lv_smem_bytes(ncrit);
     EmitOut o{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-              t.leaf_cell, ws.leaf_pfirst, ws.arrive};
+              t.leaf_cell};
     emit_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt, tiles,
                                                           ws.info, o);
     ++g_launches;

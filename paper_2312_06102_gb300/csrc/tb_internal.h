@@ -65,6 +65,7 @@ struct Workspace {
     int64_t reorder_cap = 0;
 
     float4 *xm = nullptr;            // [n] (x, y, z, m) in input order, written with the keys
+    float4 *xs = nullptr;            // [n] the same records in key order (moments)
     const float *xm_pos = nullptr;   // arrays xm was made from
     const float *xm_mass = nullptr;
     uint64_t *keys_alt = nullptr;
@@ -73,9 +74,7 @@ struct Workspace {
     uint64_t *lookback = nullptr;    // [tiles][radix]
     float *bbox_part = nullptr;      // [blocks][8]
     uint32_t *level_cnt = nullptr;   // [level tiles][kLevelFields]
-    uint32_t *arrive = nullptr;      // [cells] child-arrival counters
-    int32_t *leaf_pfirst = nullptr;  // [leaves]
-    int32_t *big_leaf = nullptr;     // [leaves] queue of leaves too big for one thread
+    int32_t *big_leaf = nullptr;     // [n] queue of depth-21 leaves too long for one thread
     DevInfo *info = nullptr;
     DevInfo *h_info = nullptr;       // pinned host mirror
 
@@ -117,13 +116,13 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int n_crit, Workspac
                           cudaStream_t s);
 cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int n_crit, Workspace &ws,
                         tb_tree &t, cudaStream_t s);
-cudaError_t launch_moments(tb_tree &t, const float *pos, const float *mass, Workspace &ws,
-                           int mode, cudaStream_t s);
+cudaError_t launch_moments(tb_tree &t, Workspace &ws, int mode, cudaStream_t s);
 cudaError_t launch_wait_selftest(int64_t limit, uint32_t *status, uint32_t *flag, cudaStream_t s);
 
 int level_tile_size();
 int64_t bbox_grid();
 SortCfg default_sort_cfg(int radix_bits);
+const SortCfg *sort_variant(int i);
 bool sort_cfg_valid(const SortCfg &c);
 
 void mark(Workspace &ws, const char *name, cudaStream_t s);

@@ -2,12 +2,14 @@
 // properties are computed as cells are created; the centre of mass of a
 // parent comes from those of its children, higher multipoles likewise).
 //
-// One thread per leaf (leaves taken in key order, so a warp reads a
-// contiguous stretch of the permutation) sums its member particles; then
-// the thread that brings the last child of a parent (an atomic arrival
-// count) combines the parent's children and climbs on.  Every parent is
-// therefore computed exactly once, from all its children in index order, so
-// the result does not depend on which thread arrives last.
+//   gather_kernel        : particles in key order, (x, y, z, m) records
+//                          (Sec. 2.3 step 3, the reorder); every thread keeps
+//                          four independent gathers in flight;
+//   level_moments_kernel : one launch per level, deepest first: a leaf sums its
+//                          contiguous members, any other cell combines its
+//                          children, which the previous launch finished;
+//   big_leaf_kernel      : depth-21 leaves of identical keys that are too long
+//                          for one thread, summed block-wide.
 //
 // Moments of a cell: M = sum m; centre of mass c = sum m x / M; central
 // second moment Q = sum m (x - c)(x - c)^T (6 components xx xy xz yy yz zz);
@@ -24,8 +26,7 @@
 //   FP32_PLAIN -- uncompensated FP32, com_lo = 0;
 //   FP64       -- FP64 accumulation; FP64 outputs beside the FP32 ones.
 // A cell of more than 2^20 particles is summed / combined in FP64 in every
-// mode.  Leaves too long for one thread (only depth-21 leaves of identical
-// keys can be) go to a queue served block-wide by a second kernel.
+// mode.
 #include "tb_device.cuh"
 
 namespace tb {
@@ -39,15 +40,11 @@ constexpr int kBigThreads = 256;
 struct MomOut {
     float *mass, *com, *com_lo, *quad, *aabb;
     double *mass64, *com64, *quad64;
-    float *pos_sorted;   // [n][4] x y z m in key order, or NULL
 };
 
 struct TreeIn {
-    const int32_t *perm, *parent, *child_first, *child_end, *pfirst, *pend;
-    const int32_t *leaf_cell, *leaf_pfirst;
-    uint32_t *arrive;
+    const int32_t *child_first, *child_end, *pfirst, *pend;
     int32_t *big_leaf;
-    int64_t n;
 };
 
 __device__ __forceinline__ int qidx(int a, int b) {
@@ -236,15 +233,13 @@ __device__ void finish_d(const MomOut &o, int64_t c, const AccD &A, const float 
 
 // ------------------------------------------------------------- leaves
 
-// Sum the members [pf, pe) of one leaf.  Member indices come from the
-// permutation; the (x, y, z, m) records are gathered eight at a time, all
-// eight loads issued before any is used, so each thread keeps several
-// independent memory requests in flight.
+// Sum the members [pf, pe) of one leaf from the key-ordered records; loads
+// are issued eight at a time before any is used.
 template <int MODE>
-__device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float4 *__restrict__ xm,
-                         int64_t c, int64_t pf, int64_t pe) {
+__device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t c, int64_t pf,
+                         int64_t pe) {
     constexpr int G = 8;
-    const float4 r0 = __ldg(xm + T.perm[pf]);
+    const float4 r0 = xs[pf];
     const float ref[3] = {r0.x, r0.y, r0.z};
     float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
     const bool f64 = MODE == TB_MOM_FP64 || (pe - pf) > kBigCell;
@@ -252,16 +247,12 @@ __device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float4 *__restr
     AccC A;
     AccP P;
     D.init(); A.init(); P.init();
-    float4 *srt = reinterpret_cast<float4 *>(o.pos_sorted);
     for (int64_t k0 = pf; k0 < pe; k0 += G) {
         const int cnt = (int)min64(G, pe - k0);
-        int32_t idx[G];
         float4 v[G];
 #pragma unroll
-        for (int j = 0; j < G; ++j) idx[j] = (j < cnt) ? __ldg(T.perm + k0 + j) : 0;
-#pragma unroll
         for (int j = 0; j < G; ++j)
-            if (j < cnt) v[j] = __ldg(xm + idx[j]);
+            if (j < cnt) v[j] = xs[k0 + j];
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             if (j >= cnt) break;
@@ -282,7 +273,6 @@ __device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float4 *__restr
                 const float dx[3] = {x[0] - ref[0], x[1] - ref[1], x[2] - ref[2]};
                 P.add(v[j].w, dx);
             }
-            if (srt) srt[k0 + j] = v[j];
         }
     }
     if (f64) finish_d(o, c, D, ref, bb, MODE == TB_MOM_FP64);
@@ -292,75 +282,78 @@ __device__ void leaf_sum(const TreeIn &T, const MomOut &o, const float4 *__restr
 
 // ----------------------------------------------------------- parents
 
+// Offset of child c's centre from the reference point ref, as a
+// double-float (h, l): (com_c - ref) + com_lo_c.
+__device__ __forceinline__ void child_offset(const MomOut &o, int64_t c, int a, float ref, float &h,
+                                             float &l) {
+    float u, v;
+    two_sum(o.com[3 * c + a], -ref, u, v);
+    v = __fadd_rn(v, o.com_lo[3 * c + a]);
+    fast_two_sum(u, v, h, l);
+}
+
 template <int MODE>
 __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
     const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
     float bb[6];
-    for (int a = 0; a < 3; ++a) { bb[a] = __ldcg(o.aabb + 6 * (int64_t)c0 + a); bb[3 + a] = __ldcg(o.aabb + 6 * (int64_t)c0 + 3 + a); }
+    for (int a = 0; a < 6; ++a) bb[a] = o.aabb[6 * (int64_t)c0 + a];
     for (int32_t c = c0 + 1; c < c1; ++c)
         for (int a = 0; a < 3; ++a) {
-            bb[a] = fminf(bb[a], __ldcg(o.aabb + 6 * (int64_t)c + a));
-            bb[3 + a] = fmaxf(bb[3 + a], __ldcg(o.aabb + 6 * (int64_t)c + 3 + a));
+            bb[a] = fminf(bb[a], o.aabb[6 * (int64_t)c + a]);
+            bb[3 + a] = fmaxf(bb[3 + a], o.aabb[6 * (int64_t)c + 3 + a]);
         }
     const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
     if (MODE == TB_MOM_FP64 || big) {
-        double M = 0.0, S[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0}, cm[8][3], mc[8];
-        int nch = 0;
-        for (int32_t c = c0; c < c1; ++c, ++nch) {
-            double Mc, com[3];
-            if (MODE == TB_MOM_FP64) {
-                Mc = __ldcg(o.mass64 + c);
-                for (int a = 0; a < 3; ++a) com[a] = __ldcg(o.com64 + 3 * (int64_t)c + a);
-            } else {
-                Mc = (double)__ldcg(o.mass + c);
-                for (int a = 0; a < 3; ++a)
-                    com[a] = (double)__ldcg(o.com + 3 * (int64_t)c + a) +
-                             (double)__ldcg(o.com_lo + 3 * (int64_t)c + a);
-            }
-            mc[nch] = Mc;
-            for (int a = 0; a < 3; ++a) cm[nch][a] = com[a];
-            M += Mc;
+        // FP64: relative to the first child's centre
+        double ref[3];
+        for (int a = 0; a < 3; ++a)
+            ref[a] = (MODE == TB_MOM_FP64) ? o.com64[3 * (int64_t)c0 + a]
+                                           : (double)o.com[3 * (int64_t)c0 + a] +
+                                                 (double)o.com_lo[3 * (int64_t)c0 + a];
+        auto cm = [&](int64_t c, int a) {
+            return (MODE == TB_MOM_FP64) ? o.com64[3 * c + a]
+                                         : (double)o.com[3 * c + a] + (double)o.com_lo[3 * c + a];
+        };
+        auto ms = [&](int64_t c) {
+            return (MODE == TB_MOM_FP64) ? o.mass64[c] : (double)o.mass[c];
+        };
+        double M = 0.0, S[3] = {0, 0, 0};
+        for (int32_t c = c0; c < c1; ++c) {
+            double mc = ms(c);
+            M += mc;
+            for (int a = 0; a < 3; ++a) S[a] += mc * (cm(c, a) - ref[a]);
         }
-        // relative to the first child's centre
-        for (int j = 0; j < nch; ++j)
-            for (int a = 0; a < 3; ++a) S[a] += mc[j] * (cm[j][a] - cm[0][a]);
-        double r[3], com[3];
+        double r[3], com[3], Q[6] = {0, 0, 0, 0, 0, 0};
         for (int a = 0; a < 3; ++a) {
             r[a] = (M != 0.0) ? S[a] / M : 0.0;
-            com[a] = cm[0][a] + r[a];
+            com[a] = ref[a] + r[a];
         }
-        for (int j = 0; j < nch; ++j) {
-            const int32_t c = c0 + j;
-            double e[3];
-            for (int a = 0; a < 3; ++a) e[a] = (cm[j][a] - cm[0][a]) - r[a];
+        for (int32_t c = c0; c < c1; ++c) {
+            double mc = ms(c), e[3];
+            for (int a = 0; a < 3; ++a) e[a] = (cm(c, a) - ref[a]) - r[a];
             int q = 0;
             for (int a = 0; a < 3; ++a)
                 for (int b = a; b < 3; ++b, ++q) {
-                    double qc = (MODE == TB_MOM_FP64) ? __ldcg(o.quad64 + 6 * (int64_t)c + q)
-                                                      : (double)__ldcg(o.quad + 6 * (int64_t)c + q);
-                    Q[q] += qc + mc[j] * e[a] * e[b];
+                    double qc = (MODE == TB_MOM_FP64) ? o.quad64[6 * (int64_t)c + q]
+                                                      : (double)o.quad[6 * (int64_t)c + q];
+                    Q[q] += qc + mc * e[a] * e[b];
                 }
         }
         write_cell_f64(o, p, M, com, Q, bb, MODE == TB_MOM_FP64);
     } else if (MODE == TB_MOM_FP32_COMP) {
         float ref[3];
-        for (int a = 0; a < 3; ++a) ref[a] = __ldcg(o.com + 3 * (int64_t)c0 + a);
+        for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
+        // pass 1: mass and first moment about ref
         float Mh = 0.f, Mc = 0.f, Sh[3] = {0, 0, 0}, Sc[3] = {0, 0, 0};
-        float dh[8][3], dl[8][3], mm[8];
-        int nch = 0;
-        for (int32_t c = c0; c < c1; ++c, ++nch) {
-            float m = __ldcg(o.mass + c), e;
-            mm[nch] = m;
+        for (int32_t c = c0; c < c1; ++c) {
+            float m = o.mass[c], e;
             two_sum(Mh, m, Mh, e);
             Mc += e;
             for (int a = 0; a < 3; ++a) {
-                float h, l;
-                two_sum(__ldcg(o.com + 3 * (int64_t)c + a), -ref[a], h, l);
-                l = __fadd_rn(l, __ldcg(o.com_lo + 3 * (int64_t)c + a));
-                fast_two_sum(h, l, dh[nch][a], dl[nch][a]);
-                float pp, pe;
-                two_prod(m, dh[nch][a], pp, pe);
-                pe = __fmaf_rn(m, dl[nch][a], pe);
+                float h, l, pp, pe;
+                child_offset(o, c, a, ref[a], h, l);
+                two_prod(m, h, pp, pe);
+                pe = __fmaf_rn(m, l, pe);
                 two_sum(Sh[a], pp, Sh[a], e);
                 Sc[a] += e + pe;
             }
@@ -374,26 +367,30 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
             if (MH != 0.f) df_div(sh, sl, MH, ML, rh[a], rl[a]);
             else rh[a] = rl[a] = 0.f;
         }
+        // pass 2: second moment with the parallel-axis shift
         float Q[6], Qc[6];
         for (int q = 0; q < 6; ++q) Q[q] = Qc[q] = 0.f;
-        for (int j = 0; j < nch; ++j) {
-            const int32_t c = c0 + j;
+        for (int32_t c = c0; c < c1; ++c) {
+            const float m = o.mass[c];
             float e[3];
-            for (int a = 0; a < 3; ++a)
-                e[a] = __fadd_rn(__fsub_rn(dh[j][a], rh[a]), __fsub_rn(dl[j][a], rl[a]));
+            for (int a = 0; a < 3; ++a) {
+                float h, l;
+                child_offset(o, c, a, ref[a], h, l);
+                e[a] = __fadd_rn(__fsub_rn(h, rh[a]), __fsub_rn(l, rl[a]));
+            }
             int q = 0;
             for (int a = 0; a < 3; ++a)
                 for (int b = a; b < 3; ++b, ++q) {
-                    float s, er;
-                    two_sum(Q[q], __ldcg(o.quad + 6 * (int64_t)c + q), s, er);
-                    Q[q] = s;
+                    float sum, er;
+                    two_sum(Q[q], o.quad[6 * (int64_t)c + q], sum, er);
+                    Q[q] = sum;
                     Qc[q] += er;
                     float t, te, pp, pe;
-                    two_prod(mm[j], e[a], t, te);
+                    two_prod(m, e[a], t, te);
                     two_prod(t, e[b], pp, pe);
                     pe = __fmaf_rn(te, e[b], pe);
-                    two_sum(Q[q], pp, s, er);
-                    Q[q] = s;
+                    two_sum(Q[q], pp, sum, er);
+                    Q[q] = sum;
                     Qc[q] += er + pe;
                 }
         }
@@ -408,22 +405,22 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
         write_cell_f32(o, p, MH + ML, ch, cl, Qf, bb);
     } else {
         float ref[3];
-        for (int a = 0; a < 3; ++a) ref[a] = __ldcg(o.com + 3 * (int64_t)c0 + a);
+        for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
         float M = 0.f, S[3] = {0, 0, 0};
         for (int32_t c = c0; c < c1; ++c) {
-            float m = __ldcg(o.mass + c);
+            float m = o.mass[c];
             M += m;
-            for (int a = 0; a < 3; ++a) S[a] += m * (__ldcg(o.com + 3 * (int64_t)c + a) - ref[a]);
+            for (int a = 0; a < 3; ++a) S[a] += m * (o.com[3 * (int64_t)c + a] - ref[a]);
         }
         float r[3];
         for (int a = 0; a < 3; ++a) r[a] = (M != 0.f) ? S[a] / M : 0.f;
         float Q[6] = {0, 0, 0, 0, 0, 0};
         for (int32_t c = c0; c < c1; ++c) {
-            float m = __ldcg(o.mass + c), e[3];
-            for (int a = 0; a < 3; ++a) e[a] = (__ldcg(o.com + 3 * (int64_t)c + a) - ref[a]) - r[a];
+            float m = o.mass[c], e[3];
+            for (int a = 0; a < 3; ++a) e[a] = (o.com[3 * (int64_t)c + a] - ref[a]) - r[a];
             int q = 0;
             for (int a = 0; a < 3; ++a)
-                for (int b = a; b < 3; ++b, ++q) Q[q] += __ldcg(o.quad + 6 * (int64_t)c + q) + m * e[a] * e[b];
+                for (int b = a; b < 3; ++b, ++q) Q[q] += o.quad[6 * (int64_t)c + q] + m * e[a] * e[b];
         }
         float ch[3], cl[3];
         for (int a = 0; a < 3; ++a) { ch[a] = ref[a] + r[a]; cl[a] = 0.f; }
@@ -431,53 +428,61 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
     }
 }
 
-// Climb from a finished cell while this thread brings the last child.
-template <int MODE>
-__device__ void climb(const TreeIn &T, const MomOut &o, int64_t c) {
-    __threadfence();
-    int64_t p = T.parent[c];
-    while (p >= 0) {
-        const uint32_t nch = (uint32_t)(T.child_end[p] - T.child_first[p]);
-        const uint32_t before = atomicAdd(&T.arrive[p], 1u);
-        if (before + 1 != nch) return;
-        __threadfence();
-        T.arrive[p] = 0;   // ready for the next moment call on this tree
-        combine_children<MODE>(T, o, p);
-        __threadfence();
-        p = T.parent[p];
+// ------------------------------------------------------------ kernels
+
+// xs[k] = xm[perm[k]]: the particles in key order.
+__global__ void __launch_bounds__(256)
+    gather_kernel(const int32_t *__restrict__ perm, const float4 *__restrict__ xm,
+                  float4 *__restrict__ xs, int64_t n, const DevInfo *info) {
+    if (info->status & kErrNonFinite) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n / 4;
+    const int4 *p4 = reinterpret_cast<const int4 *>(perm);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += stride) {
+        const int4 id = __ldcs(p4 + g);
+        const float4 a = __ldg(xm + id.x), b = __ldg(xm + id.y), c = __ldg(xm + id.z),
+                     d = __ldg(xm + id.w);
+        xs[4 * g] = a;
+        xs[4 * g + 1] = b;
+        xs[4 * g + 2] = c;
+        xs[4 * g + 3] = d;
     }
+    for (int64_t k = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+        xs[k] = __ldg(xm + perm[k]);
 }
 
+// Every cell of level d: leaves from their members, the others from their
+// children (finished by the launch for level d + 1).
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads)
-    leaf_moments_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xm, DevInfo *info) {
+    level_moments_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info, int d) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    const int64_t nl = info->n_leaves;
+    const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
-        const int64_t pf = T.leaf_pfirst[j];
-        const int64_t pe = (j + 1 < nl) ? T.leaf_pfirst[j + 1] : T.n;
-        const int64_t c = T.leaf_cell[j];
-        if (pe - pf > kBigLeafThread) {
-            uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
-            T.big_leaf[q] = (int32_t)j;
-            continue;
+    for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += stride) {
+        if (T.child_first[c] >= 0) {
+            combine_children<MODE>(T, o, c);
+        } else {
+            const int64_t pf = T.pfirst[c], pe = T.pend[c];
+            if (d == kDepthMax && pe - pf > kBigLeafThread) {
+                uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
+                T.big_leaf[q] = (int32_t)c;
+                continue;
+            }
+            leaf_sum<MODE>(o, xs, c, pf, pe);
         }
-        leaf_sum<MODE>(T, o, xm, c, pf, pe);
-        climb<MODE>(T, o, c);
     }
 }
 
-// Block-wide sums of one long leaf, then the climb.
+// Block-wide sums of the long depth-21 leaves queued by the level-21 launch.
 template <int MODE>
 __global__ void __launch_bounds__(kBigThreads)
-    big_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xm, DevInfo *info) {
+    big_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     __shared__ uint32_t s_q;
     __shared__ float s_bb[kBigThreads][6];
     __shared__ double s_d[kBigThreads][10];
     __shared__ float s_f[kBigThreads][20];
-    const int64_t nl = info->n_leaves;
     const uint32_t nq = *(volatile uint32_t *)&info->misc_ctr[2];
     for (;;) {
         if (threadIdx.x == 0) s_q = atomicAdd(&info->misc_ctr[3], 1u);
@@ -485,38 +490,32 @@ __global__ void __launch_bounds__(kBigThreads)
         const uint32_t q = s_q;
         __syncthreads();
         if (q >= nq) return;
-        const int64_t j = T.big_leaf[q];
-        const int64_t pf = T.leaf_pfirst[j];
-        const int64_t pe = (j + 1 < nl) ? T.leaf_pfirst[j + 1] : T.n;
-        const int64_t c = T.leaf_cell[j];
+        const int64_t c = T.big_leaf[q];
+        const int64_t pf = T.pfirst[c], pe = T.pend[c];
         const int64_t cnt = pe - pf;
         const int64_t chunk = (cnt + kBigThreads - 1) / kBigThreads;
         const int64_t a0 = pf + threadIdx.x * chunk, a1 = min64(pe, a0 + chunk);
-        float ref[3], x[3], m, bb[6];
-        {
-            const float4 r0 = __ldg(xm + T.perm[pf]);
-            ref[0] = r0.x; ref[1] = r0.y; ref[2] = r0.z;
-        }
-        for (int a = 0; a < 3; ++a) { bb[a] = ref[a]; bb[3 + a] = ref[a]; }
+        const float4 r0 = xs[pf];
+        const float ref[3] = {r0.x, r0.y, r0.z};
+        float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
         const bool f64 = (MODE == TB_MOM_FP64) || cnt > kBigCell;
         AccD D;
         AccC Cc;
         AccP Pp;
         D.init(); Cc.init(); Pp.init();
         for (int64_t k = a0; k < a1; ++k) {
-            const float4 v = __ldg(xm + T.perm[k]);
-            x[0] = v.x; x[1] = v.y; x[2] = v.z; m = v.w;
+            const float4 v = xs[k];
+            const float x[3] = {v.x, v.y, v.z};
             for (int a = 0; a < 3; ++a) { bb[a] = fminf(bb[a], x[a]); bb[3 + a] = fmaxf(bb[3 + a], x[a]); }
-            if (o.pos_sorted) reinterpret_cast<float4 *>(o.pos_sorted)[k] = v;
             if (f64) {
                 double dx[3];
                 for (int a = 0; a < 3; ++a) dx[a] = (double)x[a] - (double)ref[a];
-                D.add((double)m, dx);
+                D.add((double)v.w, dx);
             } else {
                 float dx[3];
                 for (int a = 0; a < 3; ++a) dx[a] = __fsub_rn(x[a], ref[a]);
-                if (MODE == TB_MOM_FP32_COMP) Cc.add(m, dx);
-                else Pp.add(m, dx);
+                if (MODE == TB_MOM_FP32_COMP) Cc.add(v.w, dx);
+                else Pp.add(v.w, dx);
             }
         }
         // tree reduction in shared memory, fixed order
@@ -589,7 +588,6 @@ __global__ void __launch_bounds__(kBigThreads)
                 for (int q2 = 0; q2 < 6; ++q2) A.Q[q2] = s_f[0][8 + q2];
                 finish_p(o, c, A, ref, bbf);
             }
-            climb<MODE>(T, o, c);
         }
         __syncthreads();
     }
@@ -606,34 +604,44 @@ __global__ void wait_selftest_kernel(int64_t limit, uint32_t *status, const uint
 }
 
 template <int MODE>
-cudaError_t moments_impl(tb_tree &t, const float *pos, const float *mass, Workspace &ws,
-                         cudaStream_t s) {
-    TreeIn T{t.perm, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-             t.leaf_cell, ws.leaf_pfirst, ws.arrive, ws.big_leaf, t.n_particles};
-    MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64,
-             t.pos_sorted};
+cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
+    TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+    MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
+    const int64_t n = t.n_particles;
     cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    int64_t grid = (t.n_particles / 4 + kMomThreads - 1) / kMomThreads;
-    if (grid > 152 * 16) grid = 152 * 16;
+    int64_t g = (n / 4 + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    gather_kernel<<<(unsigned)g, 256, 0, s>>>(t.perm, ws.xm, ws.xs, n, ws.info);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(ws, "gather", s);
+    // one persistent grid per level; a level holds at most n cells
+    int64_t grid = (n + kMomThreads - 1) / kMomThreads;
+    if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
-    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xm, ws.info);
-    ++g_launches;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xm, ws.info);
-    ++g_launches;
-    return cudaGetLastError();
+    for (int d = kDepthMax; d >= 0; --d) {
+        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xs, ws.info, d);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (d == kDepthMax) {
+            big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xs, ws.info);
+            ++g_launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    mark(ws, "moments", s);
+    return cudaSuccess;
 }
 
 }  // namespace
 
-cudaError_t launch_moments(tb_tree &t, const float *pos, const float *mass, Workspace &ws, int mode,
-                           cudaStream_t s) {
+cudaError_t launch_moments(tb_tree &t, Workspace &ws, int mode, cudaStream_t s) {
     switch (mode) {
-        case TB_MOM_FP32_COMP: return moments_impl<TB_MOM_FP32_COMP>(t, pos, mass, ws, s);
-        case TB_MOM_FP32_PLAIN: return moments_impl<TB_MOM_FP32_PLAIN>(t, pos, mass, ws, s);
-        case TB_MOM_FP64: return moments_impl<TB_MOM_FP64>(t, pos, mass, ws, s);
+        case TB_MOM_FP32_COMP: return moments_impl<TB_MOM_FP32_COMP>(t, ws, s);
+        case TB_MOM_FP32_PLAIN: return moments_impl<TB_MOM_FP32_PLAIN>(t, ws, s);
+        case TB_MOM_FP64: return moments_impl<TB_MOM_FP64>(t, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -263,19 +263,27 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
 
 }  // namespace
 
+// Compiled variants: digit bits, threads per tile, keys per thread.
+static const SortCfg kVariants[] = {
+    {8, 256, 16}, {8, 512, 12}, {8, 512, 8}, {8, 256, 8},
+    {9, 256, 16}, {9, 512, 8}, {10, 256, 16}, {10, 512, 8}, {11, 256, 16},
+};
+static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+const SortCfg *sort_variant(int i) { return (i >= 0 && i < kNumVariants) ? &kVariants[i] : nullptr; }
+
 SortCfg default_sort_cfg(int radix_bits) {
-    switch (radix_bits) {
-        case 9: return {9, 256, 16};
-        case 10: return {10, 256, 16};
-        case 11: return {11, 256, 16};
-        default: return {8, 256, 16};
-    }
+    for (int i = 0; i < kNumVariants; ++i)
+        if (kVariants[i].radix_bits == radix_bits) return kVariants[i];
+    return kVariants[0];
 }
 
 bool sort_cfg_valid(const SortCfg &c) {
-    return (c.radix_bits == 8 && c.threads == 256 && (c.items == 16 || c.items == 24)) ||
-           (c.radix_bits == 8 && c.threads == 512 && c.items == 12) ||
-           (c.radix_bits >= 9 && c.radix_bits <= 11 && c.threads == 256 && c.items == 16);
+    for (int i = 0; i < kNumVariants; ++i)
+        if (kVariants[i].radix_bits == c.radix_bits && kVariants[i].threads == c.threads &&
+            kVariants[i].items == c.items)
+            return true;
+    return false;
 }
 
 int64_t sort_tiles(const SortCfg &c, int64_t n) { return (n + c.tile() - 1) / c.tile(); }
@@ -283,15 +291,19 @@ int64_t sort_tiles(const SortCfg &c, int64_t n) { return (n + c.tile() - 1) / c.
 cudaError_t launch_sort(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int64_t n,
                         Workspace &ws, const SortCfg &cfg, uint64_t *&kout, int32_t *&pout,
                         cudaStream_t s) {
-    if (cfg.radix_bits == 8 && cfg.threads == 256 && cfg.items == 16)
-        return run_passes<8, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
-    if (cfg.radix_bits == 8 && cfg.threads == 256 && cfg.items == 24)
-        return run_passes<8, 256, 24>(ka, kb, pa, pb, n, ws, kout, pout, s);
-    if (cfg.radix_bits == 8 && cfg.threads == 512 && cfg.items == 12)
-        return run_passes<8, 512, 12>(ka, kb, pa, pb, n, ws, kout, pout, s);
-    if (cfg.radix_bits == 9) return run_passes<9, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
-    if (cfg.radix_bits == 10) return run_passes<10, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
-    if (cfg.radix_bits == 11) return run_passes<11, 256, 16>(ka, kb, pa, pb, n, ws, kout, pout, s);
+#define TB_SORT_CASE(B, T, I)                                             \
+    if (cfg.radix_bits == B && cfg.threads == T && cfg.items == I)        \
+        return run_passes<B, T, I>(ka, kb, pa, pb, n, ws, kout, pout, s);
+    TB_SORT_CASE(8, 256, 16)
+    TB_SORT_CASE(8, 512, 12)
+    TB_SORT_CASE(8, 512, 8)
+    TB_SORT_CASE(8, 256, 8)
+    TB_SORT_CASE(9, 256, 16)
+    TB_SORT_CASE(9, 512, 8)
+    TB_SORT_CASE(10, 256, 16)
+    TB_SORT_CASE(10, 512, 8)
+    TB_SORT_CASE(11, 256, 16)
+#undef TB_SORT_CASE
     return cudaErrorInvalidValue;
 }
 
