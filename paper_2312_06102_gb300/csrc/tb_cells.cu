@@ -16,176 +16,134 @@
 // per-depth merges of Alg. 2 by one pass over the particles.
 //
 // Canonical order is level-major, key (= first particle) ascending within a
-// level, so the index of cell (d, k) is level_offset[d] plus the number of
-// level-d starts before k: a 22-way prefix count, done in three launches:
-//   level_count_kernel : per tile of particles, the number of cells started at
-//                        each level and the number of leaves started;
+// level, so the index of cell (d, k) is level_offset[d] + P_d(k), P_d(k) the
+// number of level-d starts before k: a 22-way prefix count, done in three
+// launches over tiles of 1024 particles, one particle per thread:
+//   level_count_kernel : per tile, the cells started at each level and the
+//                        leaves started (one warp ballot per level);
 //   level_scan_kernel  : per level, prefix over tiles; the last block forms the
 //                        level offsets, the cell count and the depth;
 //   emit_kernel        : re-derives m and L, and writes every cell.
-// Links follow from the same counts:
-//   parent of (d, k)       = the level-(d-1) cell holding k: index P[d-1] - 1
-//                            once k's own shallower cells are counted;
-//   child_first of (d, k)  = (d+1, k) when d < L_k: index P[d+1];
+// Links follow from the same counts (P_d(k) before k's own starts):
+//   index of (d, k)        = P_d(k);
+//   parent of (d, k)       = (d-1, k) = P_{d-1}(k) if d > m_k, else the level-(d-1)
+//                            cell holding k, started earlier: P_{d-1}(k) - 1;
+//   child_first of (d, k)  = (d+1, k) = P_{d+1}(k) when d < L_k;
 //   pend, child_end        = written by the leaf start k' that closes the cell:
 //                            k' closes levels m_k' .. L_{k'-1} (the cells holding
-//                            k'-1 but not k'); the last particle closes all.
+//                            k'-1 but not k'), cell P_d(k') - 1, child_end
+//                            P_{d+1}(k'); the last particle closes all.
 // No cell is written twice and no pass over the cells is needed afterwards.
+// L_k, a maximum over a window of n + 1 values of c, comes from a doubling
+// table: M_1 = c, M_2q[i] = max(M_q[i], M_q[i+q]); with p the largest power of
+// two <= n + 1, L_k = max(M_p[k-n], M_p[k-p+1]).
 #include "tb_device.cuh"
 
 namespace tb {
 
 namespace {
 
-constexpr int kLvThreads = 256;
-constexpr int kLvItems = 16;
-constexpr int kLvTile = kLvThreads * kLvItems;
+constexpr int kLvThreads = 1024;
+constexpr int kLvWarps = kLvThreads / 32;
+constexpr int kLvTile = kLvThreads;   // one particle per thread
 
-// Shared-memory layout of one level tile.
-struct LvSmem {
-    uint64_t *key;   // keys of [s - n - 1, e + n)
-    uint8_t *c;      // c_i over [s - n - 1, e)
-    uint8_t *pm;     // prefix max within blocks of n + 1
-    uint8_t *sm;     // suffix max within blocks of n + 1
-    uint8_t *L;      // L_k over [s - 1, e)        (index k - s + 1)
-    uint8_t *m;      // m_k over [s, e)            (index k - s), padded to kLvTile
-};
+__host__ __device__ inline int lv_pow2(int ncrit) {
+    int p = 1;
+    while (2 * p <= ncrit + 1) p *= 2;
+    return p;
+}
 
 __host__ __device__ inline size_t lv_smem_bytes(int ncrit) {
-    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
-    size_t b = (ext * 8 + 15) & ~size_t(15);   // keys, padded to 16 bytes
-    b += 3 * ((ext + 15) & ~size_t(15));       // c, pm, sm
-    b += (kLvTile + 16) + kLvTile;       // L, m
-    return b + 64;
+    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;   // keys of [s-n-1, e+n)
+    size_t nc = (size_t)kLvTile + ncrit + 1;                // c over [s-n-1, e)
+    return ((ext * 8 + 15) & ~size_t(15)) + 2 * ((nc + 15) & ~size_t(15)) + 64;
 }
 
-__device__ inline LvSmem lv_carve(unsigned char *raw, int ncrit) {
-    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
-    size_t extp = (ext + 15) & ~size_t(15);
-    LvSmem s;
-    s.key = reinterpret_cast<uint64_t *>(raw);
-    unsigned char *p = raw + ((ext * 8 + 15) & ~size_t(15));   // every region 16-byte aligned
-    s.c = p; p += extp;
-    s.pm = p; p += extp;
-    s.sm = p; p += extp;
-    s.L = p; p += kLvTile + 16;
-    s.m = p;
-    return s;
-}
+struct Front {
+    int m, L, Lprev;      // this thread's particle k (m = 255 beyond the tile)
+    int64_t k;
+};
 
-// m and L for every particle of the tile [s, e) (plus L of s - 1), into
-// shared memory.  Out-of-range neighbours contribute nothing.
-__device__ void tile_levels(const uint64_t *__restrict__ skeys, int64_t n, int ncrit, int64_t s,
-                            int64_t e, const LvSmem &sm) {
-    const int64_t ext_lo = s - ncrit - 1;
-    const int next = (int)(e + ncrit - ext_lo);     // keys held
-    const int nc = (int)(e - ext_lo);               // c values held
+// Shared state of one tile: masks and counts per warp and field
+// (fields 0..21 = cell starts per level, 22 = leaf starts).
+struct TileShared {
+    uint32_t mask[kLvWarps][kLevelFields];
+    uint32_t base[kLevelFields];
+};
+
+// m, L and L of the previous particle for particle s + threadIdx.x, and the
+// ballot masks of the level starts of every warp.
+__device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t n, int ncrit, int64_t s,
+                            int64_t e, unsigned char *raw, TileShared &ts) {
+    const int64_t lo = s - ncrit - 1;
+    const int next = (int)(e + ncrit - lo);
+    const int nc = (int)(e - lo);
+    const size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
+    const size_t ncp = ((size_t)kLvTile + ncrit + 1 + 15) & ~size_t(15);
+    uint64_t *key = reinterpret_cast<uint64_t *>(raw);
+    uint8_t *A = raw + ((ext * 8 + 15) & ~size_t(15));
+    uint8_t *B = A + ncp;
     for (int x = threadIdx.x; x < next; x += blockDim.x) {
-        int64_t i = ext_lo + x;
-        sm.key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
+        const int64_t i = lo + x;
+        key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
     }
     __syncthreads();
     for (int x = threadIdx.x; x < nc; x += blockDim.x) {
-        int64_t i = ext_lo + x;
+        const int64_t i = lo + x;
         int v = 0;
-        if (i >= 0 && i + ncrit < n) v = min(kDepthMax, min_depth(sm.key[x], sm.key[x + ncrit]));
-        sm.c[x] = (uint8_t)v;
+        if (i >= 0 && i + ncrit < n) v = min(kDepthMax, min_depth(key[x], key[x + ncrit]));
+        A[x] = (uint8_t)v;
     }
     __syncthreads();
-    // running max inside consecutive blocks of w = n + 1 c-values
-    const int w = ncrit + 1;
-    const int nblk = (nc + w - 1) / w;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        int lo = b * w, hi = min(nc, lo + w);
-        uint8_t run = 0;
-        for (int x = lo; x < hi; ++x) { run = max(run, sm.c[x]); sm.pm[x] = run; }
-        run = 0;
-        for (int x = hi - 1; x >= lo; --x) { run = max(run, sm.c[x]); sm.sm[x] = run; }
+    const int p = lv_pow2(ncrit);
+    for (int q = 1; q < p; q *= 2) {
+        for (int x = threadIdx.x; x < nc; x += blockDim.x)
+            B[x] = (x + q < nc) ? max(A[x], A[x + q]) : A[x];
+        __syncthreads();
+        uint8_t *t = A; A = B; B = t;
     }
-    __syncthreads();
-    // L_i = max(c over [i-n, i]) = max(suffix max at i-n, prefix max at i)
-    const int nL = (int)(e - s + 1);
-    for (int y = threadIdx.x; y < kLvTile + 16; y += blockDim.x) {
-        if (y < nL) {
-            int x1 = y + ncrit;          // i - ext_lo for i = s - 1 + y
-            int x0 = y;                  // (i - n) - ext_lo
-            sm.L[y] = max(sm.sm[x0], sm.pm[x1]);
-        } else {
-            sm.L[y] = 0;                 // beyond the tile: with m = 255 starts nothing
-        }
+    // A[x] = max of c over [x, x + p) (truncated at the end)
+    Front f;
+    f.k = s + threadIdx.x;
+    auto window = [&](int64_t k) {   // max c over [k - n, k], k in [s - 1, e)
+        const int x0 = (int)(k - ncrit - lo), x1 = (int)(k - p + 1 - lo);
+        return (int)max(A[x0], A[x1]);
+    };
+    if (f.k < e) {
+        const int x = (int)(f.k - lo);
+        f.m = (f.k == 0) ? 0 : min_depth(key[x - 1], key[x]);
+        f.L = window(f.k);
+        f.Lprev = window(f.k - 1);
+    } else {
+        f.m = 255;
+        f.L = 0;
+        f.Lprev = 0;
     }
-    const int nm = (int)(e - s);
-    for (int y = threadIdx.x; y < kLvTile; y += blockDim.x) {
-        uint8_t v = 0;
-        if (y < nm) {
-            int64_t k = s + y;
-            int x = (int)(k - ext_lo);
-            v = (k == 0) ? 0 : (uint8_t)min_depth(sm.key[x - 1], sm.key[x]);
-        } else {
-            v = 255;   // beyond the tile: starts nothing
-        }
-        sm.m[y] = v;
-    }
-    __syncthreads();
-}
-
-// Per-thread counts of cell starts per level (fields 0..21) and leaf starts
-// (field 22), 5 bits per field (a thread owns 16 particles), packed in two
-// 64-bit words.
-struct Packed {
-    uint64_t a, b;
-    __device__ void add(int f) {
-        if (f < 12) a += 1ull << (5 * f);
-        else b += 1ull << (5 * (f - 12));
-    }
-    __device__ uint32_t get(int f) const {
-        return f < 12 ? (uint32_t)((a >> (5 * f)) & 31u) : (uint32_t)((b >> (5 * (f - 12))) & 31u);
-    }
-};
-
-__device__ inline void load_items(const LvSmem &sm, uint8_t (&mm)[kLvItems], uint8_t (&LL)[kLvItems],
-                                  uint8_t &Lprev) {
-    const int y0 = threadIdx.x * kLvItems;
-    uint4 mv = *reinterpret_cast<const uint4 *>(sm.m + y0);
-    // L is stored from s - 1: L[y0 + 1 + j] is the item j, L[y0] the one before
-    uint8_t lraw[kLvItems + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j <= kLvItems; ++j) lraw[j] = sm.L[y0 + j];
-    const uint8_t *mb = reinterpret_cast<const uint8_t *>(&mv);
-#pragma unroll
-    for (int j = 0; j < kLvItems; ++j) { mm[j] = mb[j]; LL[j] = lraw[j + 1]; }
-    Lprev = lraw[0];
+    for (int d = 0; d < kLevels; ++d) {
+        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
+        if (lane == 0) ts.mask[warp][d] = mk;
+    }
+    const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
+    if (lane == 0) ts.mask[warp][kLevels] = lm;
+    __syncthreads();
+    return f;
 }
 
 __global__ void __launch_bounds__(kLvThreads)
     level_count_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
                        uint32_t *__restrict__ tile_cnt, int64_t n_tiles) {
     extern __shared__ __align__(16) unsigned char raw[];
-    LvSmem sm = lv_carve(raw, ncrit);
+    __shared__ TileShared ts;
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    tile_levels(skeys, n, ncrit, s, e, sm);
-    uint8_t mm[kLvItems], LL[kLvItems], Lp;
-    load_items(sm, mm, LL, Lp);
-    Packed pc{0, 0};
-#pragma unroll
-    for (int j = 0; j < kLvItems; ++j) {
-        int m = mm[j], L = LL[j];
-        for (int d = m; d <= L; ++d) pc.add(d);
-        if (m <= L) pc.add(kLevels);
+    tile_front(skeys, n, ncrit, s, e, raw, ts);
+    if (threadIdx.x < kLevelFields) {
+        uint32_t sum = 0;
+        for (int w = 0; w < kLvWarps; ++w) sum += __popc(ts.mask[w][threadIdx.x]);
+        tile_cnt[(int64_t)threadIdx.x * n_tiles + t] = sum;
     }
-    // block sums of the 23 fields
-    __shared__ uint32_t s_tot[kLevelFields];
-    if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int f = 0; f < kLevelFields; ++f) {
-        uint32_t v = pc.get(f);
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_tot[f], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < kLevelFields) tile_cnt[(int64_t)threadIdx.x * n_tiles + t] = s_tot[threadIdx.x];
 }
 
 // One block per field: exclusive prefix over tiles (in place); the last block
@@ -263,83 +221,59 @@ __global__ void __launch_bounds__(kLvThreads)
                 EmitOut out) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     extern __shared__ __align__(16) unsigned char raw[];
-    LvSmem sm = lv_carve(raw, ncrit);
-    // P[f][thread]: running start counts, laid out field-major (no bank conflicts)
-    __shared__ uint32_t s_P[kLevelFields][kLvThreads];
-    __shared__ uint32_t s_wsum[kLvThreads / 32][kLevelFields];
+    __shared__ TileShared ts;
+    __shared__ uint32_t woff[kLvWarps][kLevelFields];
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    tile_levels(skeys, n, ncrit, s, e, sm);
-    uint8_t mm[kLvItems], LL[kLvItems], Lp;
-    load_items(sm, mm, LL, Lp);
-    Packed pc{0, 0};
-#pragma unroll
-    for (int j = 0; j < kLvItems; ++j) {
-        int m = mm[j], L = LL[j];
-        for (int d = m; d <= L; ++d) pc.add(d);
-        if (m <= L) pc.add(kLevels);
-    }
-    // exclusive scan over threads of every field
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl[kLevelFields];
-#pragma unroll
-    for (int f = 0; f < kLevelFields; ++f) {
-        uint32_t v = pc.get(f), x = v;
-        for (int off = 1; off < 32; off <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane >= off) x += y;
+    const Front f = tile_front(skeys, n, ncrit, s, e, raw, ts);
+    // exclusive prefix of the per-warp counts, and the tile's global base
+    if (threadIdx.x < kLevelFields) {
+        const int fld = threadIdx.x;
+        uint32_t run = 0;
+        for (int w = 0; w < kLvWarps; ++w) {
+            woff[w][fld] = run;
+            run += __popc(ts.mask[w][fld]);
         }
-        incl[f] = x - v;   // exclusive within the warp
-        if (lane == 31) s_wsum[warp][f] = x;
+        ts.base[fld] = ((fld < kLevels) ? (uint32_t)info->level_offset[fld] : 0u) +
+                       tile_off[(int64_t)fld * n_tiles + t];
     }
     __syncthreads();
-#pragma unroll
-    for (int f = 0; f < kLevelFields; ++f) {
-        uint32_t wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += s_wsum[w][f];
-        uint32_t base = (f < kLevels) ? (uint32_t)info->level_offset[f] : 0u;
-        s_P[f][threadIdx.x] = base + tile_off[(int64_t)f * n_tiles + t] + wpre + incl[f];
-    }
-    __syncthreads();
-
-    const int64_t k0 = s + (int64_t)threadIdx.x * kLvItems;
-    const uint64_t *keyp = sm.key + (k0 - (s - ncrit - 1));
-#pragma unroll 1
-    for (int j = 0; j < kLvItems; ++j) {
-        const int64_t k = k0 + j;
-        if (k >= e) break;
-        const int m = mm[j], L = LL[j];
-        const int Lprev = (j == 0) ? Lp : LL[j - 1];
+    if (f.k >= e) return;
+    const int warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    // P_d(k): level-d starts before k, as a global cell index
+    auto P = [&](int d) {
+        return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
+    };
+    const int64_t k = f.k;
+    const int m = f.m, L = f.L;
+    if (k > 0) {
         // close the cells holding k-1 but not k
-        if (k > 0) {
-            for (int d = m; d <= Lprev; ++d) {
-                int32_t idx = (int32_t)s_P[d][threadIdx.x] - 1;
-                out.pend[idx] = (int32_t)k;
-                out.child_end[idx] = (d < Lprev) ? (int32_t)s_P[d + 1][threadIdx.x] : -1;
-            }
+        for (int d = m; d <= f.Lprev; ++d) {
+            const uint32_t idx = P(d) - 1;
+            out.pend[idx] = (int32_t)k;
+            out.child_end[idx] = (d < f.Lprev) ? (int32_t)P(d + 1) : -1;
         }
-        // open k's cells, shallowest first
-        if (m <= L) {
-            const uint64_t K = keyp[j];
-            for (int d = m; d <= L; ++d) {
-                int32_t idx = (int32_t)s_P[d][threadIdx.x];
-                out.ckey[idx] = cell_key(K, d);
-                out.level[idx] = (uint8_t)d;
-                out.pfirst[idx] = (int32_t)k;
-                out.parent[idx] = (d == 0) ? -1 : (int32_t)s_P[d - 1][threadIdx.x] - 1;
-                out.child_first[idx] = (d < L) ? (int32_t)s_P[d + 1][threadIdx.x] : -1;
-                s_P[d][threadIdx.x] = (uint32_t)idx + 1;
-            }
-            uint32_t leaf = s_P[kLevels][threadIdx.x];
-            out.leaf_cell[leaf] = (int32_t)s_P[L][threadIdx.x] - 1;
-            s_P[kLevels][threadIdx.x] = leaf + 1;
+    }
+    if (m <= L) {
+        const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[k - (s - ncrit - 1)];
+        for (int d = m; d <= L; ++d) {
+            const uint32_t idx = P(d);
+            out.ckey[idx] = cell_key(K, d);
+            out.level[idx] = (uint8_t)d;
+            out.pfirst[idx] = (int32_t)k;
+            out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == m ? 1 : 0);
+            out.child_first[idx] = (d < L) ? (int32_t)P(d + 1) : -1;
         }
-        if (k == n - 1) {
-            for (int d = 0; d <= L; ++d) {
-                int32_t idx = (int32_t)s_P[d][threadIdx.x] - 1;
-                out.pend[idx] = (int32_t)n;
-                out.child_end[idx] = (d < L) ? (int32_t)s_P[d + 1][threadIdx.x] : -1;
-            }
+        out.leaf_cell[P(kLevels)] = (int32_t)P(L);
+    }
+    if (k == n - 1) {
+        // the last particle closes every cell holding it
+        for (int d = 0; d <= L; ++d) {
+            const uint32_t own = (m <= d) ? 1u : 0u;
+            const uint32_t idx = P(d) + own - 1;
+            out.pend[idx] = (int32_t)n;
+            out.child_end[idx] = (d < L) ? (int32_t)(P(d + 1) + ((m <= d + 1) ? 1u : 0u)) : -1;
         }
     }
 }

@@ -27,6 +27,8 @@
 //   FP64       -- FP64 accumulation; FP64 outputs beside the FP32 ones.
 // A cell of more than 2^20 particles is summed / combined in FP64 in every
 // mode.
+#include <type_traits>
+
 #include "tb_device.cuh"
 
 namespace tb {
@@ -234,19 +236,20 @@ __device__ void finish_d(const MomOut &o, int64_t c, const AccD &A, const float 
 // ------------------------------------------------------------- leaves
 
 // Sum the members [pf, pe) of one leaf from the key-ordered records; loads
-// are issued eight at a time before any is used.
+// are issued four at a time before any is used.  Leaves reaching this path
+// hold at most 2048 particles (longer ones, only possible at depth 21, go to
+// big_leaf_kernel), so the FP32 modes never need the FP64 route here.
 template <int MODE>
 __device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t c, int64_t pf,
                          int64_t pe) {
-    constexpr int G = 8;
+    constexpr int G = 4;
     const float4 r0 = xs[pf];
     const float ref[3] = {r0.x, r0.y, r0.z};
     float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
-    const bool f64 = MODE == TB_MOM_FP64 || (pe - pf) > kBigCell;
-    AccD D;
-    AccC A;
-    AccP P;
-    D.init(); A.init(); P.init();
+    typename std::conditional<MODE == TB_MOM_FP64, AccD,
+                              typename std::conditional<MODE == TB_MOM_FP32_COMP, AccC,
+                                                        AccP>::type>::type A;
+    A.init();
     for (int64_t k0 = pf; k0 < pe; k0 += G) {
         const int cnt = (int)min64(G, pe - k0);
         float4 v[G];
@@ -261,23 +264,23 @@ __device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t
                 bb[a] = fminf(bb[a], x[a]);
                 bb[3 + a] = fmaxf(bb[3 + a], x[a]);
             }
-            if (f64) {
+            if constexpr (MODE == TB_MOM_FP64) {
                 const double dx[3] = {(double)x[0] - (double)ref[0], (double)x[1] - (double)ref[1],
                                       (double)x[2] - (double)ref[2]};
-                D.add((double)v[j].w, dx);
-            } else if (MODE == TB_MOM_FP32_COMP) {
+                A.add((double)v[j].w, dx);
+            } else if constexpr (MODE == TB_MOM_FP32_COMP) {
                 const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
                                      __fsub_rn(x[2], ref[2])};
                 A.add(v[j].w, dx);
             } else {
                 const float dx[3] = {x[0] - ref[0], x[1] - ref[1], x[2] - ref[2]};
-                P.add(v[j].w, dx);
+                A.add(v[j].w, dx);
             }
         }
     }
-    if (f64) finish_d(o, c, D, ref, bb, MODE == TB_MOM_FP64);
-    else if (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
-    else finish_p(o, c, P, ref, bb);
+    if constexpr (MODE == TB_MOM_FP64) finish_d(o, c, A, ref, bb, true);
+    else if constexpr (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
+    else finish_p(o, c, A, ref, bb);
 }
 
 // ----------------------------------------------------------- parents
@@ -292,18 +295,12 @@ __device__ __forceinline__ void child_offset(const MomOut &o, int64_t c, int a, 
     fast_two_sum(u, v, h, l);
 }
 
+// Children [c0, c1) of p combined in FP64 (FP64 mode, or a cell of more
+// than 2^20 particles in the FP32 modes).  Kept out of line so that its
+// registers do not weigh on the FP32 path.
 template <int MODE>
-__device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
-    const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
-    float bb[6];
-    for (int a = 0; a < 6; ++a) bb[a] = o.aabb[6 * (int64_t)c0 + a];
-    for (int32_t c = c0 + 1; c < c1; ++c)
-        for (int a = 0; a < 3; ++a) {
-            bb[a] = fminf(bb[a], o.aabb[6 * (int64_t)c + a]);
-            bb[3 + a] = fmaxf(bb[3 + a], o.aabb[6 * (int64_t)c + 3 + a]);
-        }
-    const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
-    if (MODE == TB_MOM_FP64 || big) {
+__device__ __noinline__ void combine_f64(const MomOut &o, int64_t p, int32_t c0, int32_t c1,
+                                         const float bb[6]) {
         // FP64: relative to the first child's centre
         double ref[3];
         for (int a = 0; a < 3; ++a)
@@ -340,7 +337,22 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
                 }
         }
         write_cell_f64(o, p, M, com, Q, bb, MODE == TB_MOM_FP64);
-    } else if (MODE == TB_MOM_FP32_COMP) {
+}
+
+template <int MODE>
+__device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
+    const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
+    float bb[6];
+    for (int a = 0; a < 6; ++a) bb[a] = o.aabb[6 * (int64_t)c0 + a];
+    for (int32_t c = c0 + 1; c < c1; ++c)
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(bb[a], o.aabb[6 * (int64_t)c + a]);
+            bb[3 + a] = fmaxf(bb[3 + a], o.aabb[6 * (int64_t)c + 3 + a]);
+        }
+    const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
+    if (MODE == TB_MOM_FP64 || big) {
+        combine_f64<MODE>(o, p, c0, c1, bb);
+    } else if constexpr (MODE == TB_MOM_FP32_COMP) {
         float ref[3];
         for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
         // pass 1: mass and first moment about ref
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(256)
 // Every cell of level d: leaves from their members, the others from their
 // children (finished by the launch for level d + 1).
 template <int MODE>
-__global__ void __launch_bounds__(kMomThreads)
+__global__ void __launch_bounds__(kMomThreads, 3)
     level_moments_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info, int d) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];

@@ -25,6 +25,7 @@ namespace tb {
 namespace {
 
 constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr int kLookWindow = 8;
 constexpr uint64_t kFlagIncl = 2ull << 62;
 
 template <int RADIX_BITS, int THREADS, int ITEMS>
@@ -157,41 +158,16 @@ __global__ void __launch_bounds__(THREADS)
     }
     __syncthreads();
 
-    // decoupled look-back, one digit per thread
+    // publish this tile's digit counts (aggregate), then order the tile by
+    // digit in shared memory while the predecessors finish theirs
     const uint64_t epoch = (uint64_t)((info->epoch + (uint32_t)pass) & 0x3fffffffu);
 #pragma unroll
     for (int r = 0; r < (RADIX + THREADS - 1) / THREADS; ++r) {
         int d = r * THREADS + threadIdx.x;
         if (d >= RADIX) continue;
-        uint32_t cnt = my_count[r];
         uint64_t *slot = lookback + (int64_t)tile * RADIX + d;
-        uint32_t excl = 0;
-        if (tile == 0) {
-            st_relaxed_u64(slot, kFlagIncl | (epoch << 32) | cnt);
-        } else {
-            st_relaxed_u64(slot, kFlagAgg | (epoch << 32) | cnt);
-            int64_t pred = (int64_t)tile - 1;
-            int64_t iter = 0;
-            while (pred >= 0) {
-                uint64_t w = ld_relaxed_u64(lookback + pred * RADIX + d);
-                if (((w >> 32) & 0x3fffffffu) != epoch || (w >> 62) == 0) {
-                    if (!poll_backoff(iter, spin_limit)) {
-                        flag_error(&info->status, kErrTimeout);
-                        break;
-                    }
-                    continue;
-                }
-                excl += (uint32_t)w;
-                if ((w >> 62) == 2) break;
-                --pred;
-            }
-            st_relaxed_u64(slot, kFlagIncl | (epoch << 32) | (excl + cnt));
-        }
-        sm.glob_base[d] = digit_off[d] + excl - sm.tile_off[d];
+        st_relaxed_u64(slot, (tile == 0 ? kFlagIncl : kFlagAgg) | (epoch << 32) | my_count[r]);
     }
-    __syncthreads();
-
-    // order the tile by digit in shared memory
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int e = wbase + i * 32 + lane;
@@ -201,6 +177,47 @@ __global__ void __launch_bounds__(THREADS)
             sm.keys[p] = key[i];
             sm.vals[p] = val[i];
         }
+    }
+
+    // decoupled look-back, one digit per thread, kLookWindow predecessors
+    // read per round so that one memory latency covers several tiles
+#pragma unroll
+    for (int r = 0; r < (RADIX + THREADS - 1) / THREADS; ++r) {
+        int d = r * THREADS + threadIdx.x;
+        if (d >= RADIX) continue;
+        uint32_t excl = 0;
+        if (tile > 0) {
+            int64_t pred = (int64_t)tile - 1;
+            int64_t iter = 0;
+            for (;;) {
+                uint64_t w[kLookWindow];
+#pragma unroll
+                for (int j = 0; j < kLookWindow; ++j)
+                    w[j] = (pred - j >= 0) ? ld_relaxed_u64(lookback + (pred - j) * RADIX + d) : 0ull;
+                int adv = 0;
+                bool found = false, blocked = false;
+#pragma unroll
+                for (int j = 0; j < kLookWindow; ++j) {
+                    if (found || blocked) continue;
+                    if (pred - j < 0 || ((w[j] >> 32) & 0x3fffffffu) != epoch || (w[j] >> 62) == 0) {
+                        blocked = true;
+                        continue;
+                    }
+                    excl += (uint32_t)w[j];
+                    adv = j + 1;
+                    if ((w[j] >> 62) == 2) found = true;
+                }
+                if (found) break;
+                pred -= adv;
+                if (adv == 0 && !poll_backoff(iter, spin_limit)) {
+                    flag_error(&info->status, kErrTimeout);
+                    break;
+                }
+            }
+            st_relaxed_u64(lookback + (int64_t)tile * RADIX + d,
+                           kFlagIncl | (epoch << 32) | (excl + my_count[r]));
+        }
+        sm.glob_base[d] = digit_off[d] + excl - sm.tile_off[d];
     }
     __syncthreads();
 
