@@ -292,6 +292,10 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int ncrit, Workspace
                              (int)lv_smem_bytes(kMaxNcrit));
         cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lv_smem_bytes(kMaxNcrit));
+        cudaFuncSetAttribute(level_count_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     level_count_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt,

@@ -43,7 +43,7 @@ struct SortSmem {
 };
 
 template <int RADIX_BITS, int THREADS, int ITEMS, bool FIRST>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 2 : 1))
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
                     int pass, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
@@ -252,6 +252,12 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(onesweep_kernel<B, T, I, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(onesweep_kernel<B, T, I, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(onesweep_kernel<B, T, I, false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     const int64_t tiles = (n + S::TILE - 1) / S::TILE;
