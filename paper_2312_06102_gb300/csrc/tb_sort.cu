@@ -7,8 +7,8 @@
 // (Adinets & Merrill 2022):
 //   - every block takes the next tile id from an atomic counter, so a block
 //     only ever waits on tiles that blocks already running own;
-//   - it ranks its tile's digits stably, warp by warp (warp match + popc),
-//     in tile order;
+//   - it ranks its tile's digits stably, warp by warp (ballot peer masks,
+//     shared-memory counters), in tile order;
 //   - it publishes its per-digit counts to a look-back array and walks back
 //     over earlier tiles until it meets an inclusive prefix (decoupled
 //     look-back); every wait is bounded and reports a timeout instead of
@@ -43,7 +43,7 @@ struct SortSmem {
 };
 
 template <int RADIX_BITS, int THREADS, int ITEMS, bool FIRST>
-__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2) : (ITEMS <= 8 ? 2 : 1)))
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
                     int pass, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
@@ -83,23 +83,33 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 2 : 1))
         }
     }
 
-    // stable rank within the warp, in element order
+    // stable rank within the warp, in element order.  The lanes holding the
+    // same digit are found with one ballot per digit bit (plus one for the
+    // tail sentinel); the lowest of them adds the group's size to the warp's
+    // digit counter with a shared-memory atomic, whose returned old value is
+    // collected only after every item has been issued, so no item waits on
+    // the one before.  A warp's atomics on one counter are applied in issue
+    // order, which keeps equal digits in element order.
     const unsigned lt = lanemask_lt();
+    uint32_t old_cnt[ITEMS], lead_rank[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        int e = wbase + i * 32 + lane;
-        uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        uint32_t before = 0;
-        if (lane == leader) {
-            before = sm.warp_hist[warp][d];
-            sm.warp_hist[warp][d] = before + __popc(peers);
+        const int e = wbase + i * 32 + lane;
+        const uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= RADIX_BITS; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned v = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? v : ~v;
         }
-        before = __shfl_sync(0xffffffffu, before, leader);
-        rank[i] = before + __popc(peers & lt);
-        __syncwarp();
+        const int leader = __ffs(peers) - 1;
+        old_cnt[i] = (lane == leader) ? atomicAdd(&sm.warp_hist[warp][d], (uint32_t)__popc(peers)) : 0u;
+        lead_rank[i] = (uint32_t)leader | ((uint32_t)__popc(peers & lt) << 8);
     }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+        rank[i] = __shfl_sync(0xffffffffu, old_cnt[i], lead_rank[i] & 31u) + (lead_rank[i] >> 8);
     __syncthreads();
 
     // per-digit: offsets of each warp within the digit, tile digit counts
@@ -288,8 +298,8 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
 
 // Compiled variants: digit bits, threads per tile, keys per thread.
 static const SortCfg kVariants[] = {
-    {8, 256, 16}, {8, 512, 12}, {8, 512, 8}, {8, 256, 8},
-    {9, 256, 16}, {9, 512, 8}, {10, 256, 16}, {10, 512, 8}, {11, 256, 16},
+    {8, 256, 16}, {8, 512, 16}, {8, 512, 12}, {8, 512, 8}, {8, 256, 8},
+    {9, 256, 16}, {9, 512, 16}, {9, 512, 8}, {10, 256, 16}, {10, 512, 8}, {11, 256, 16},
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -318,10 +328,12 @@ cudaError_t launch_sort(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, in
     if (cfg.radix_bits == B && cfg.threads == T && cfg.items == I)        \
         return run_passes<B, T, I>(ka, kb, pa, pb, n, ws, kout, pout, s);
     TB_SORT_CASE(8, 256, 16)
+    TB_SORT_CASE(8, 512, 16)
     TB_SORT_CASE(8, 512, 12)
     TB_SORT_CASE(8, 512, 8)
     TB_SORT_CASE(8, 256, 8)
     TB_SORT_CASE(9, 256, 16)
+    TB_SORT_CASE(9, 512, 16)
     TB_SORT_CASE(9, 512, 8)
     TB_SORT_CASE(10, 256, 16)
     TB_SORT_CASE(10, 512, 8)
