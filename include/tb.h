@@ -203,6 +203,28 @@ const char *tb_stage_name(tb_tree *tree, int32_t i);
  * TB_ETIMEOUT when the wait ran out and the context is still usable. */
 tb_status tb_selftest_wait(int64_t spin_limit, tb_stream stream);
 
+/* Allocation-free keys and sort (this entry point has no counterpart in the
+ * paper; it exists for callers of this library that cannot allocate device
+ * memory at call time -- for example code running while another component's
+ * caching allocator holds the device's free memory, or inside a loop that
+ * must not pay cudaMalloc's implicit synchronisation).
+ * Computes the same root cube, keys and stable (key, index) sort as tb_build
+ * (Sec. 2.2, Sec. 2.3 steps 1 and 2):
+ *   d_pos   [n][3] FP32 positions (device, caller-owned)
+ *   n       0 <= n <= TB_NOALLOC_MAX_N, else TB_EINVAL before any GPU work
+ *   d_pkey  [n] out: sorted keys (device, caller-owned, 8-byte aligned)
+ *   d_perm  [n] out: original index of each sorted key (device, caller-owned)
+ *   h_root  [4] out, host, optional: root corner x y z and side
+ * Scratch lives in one fixed file-scope device array (about 15 MB per GPU
+ * that loads the library, held until exit); nothing is allocated.  The first
+ * call on a device looks up that array's address with the device current.
+ * Every call shares the array, so calls whose GPU work overlaps race; order
+ * them on one stream.  The call synchronises `stream` before it returns
+ * TB_OK, TB_EINVAL, TB_ECUDA, TB_ENONFINITE or TB_ETIMEOUT. */
+#define TB_NOALLOC_MAX_N 524288
+tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint64_t *d_pkey, int32_t *d_perm,
+                                 double *h_root, tb_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,9 @@ from ._lib import (  # noqa: F401
     Tree,
     build,
     build_batched,
+    NOALLOC_MAX_N,
     kernel_launches,
+    keys_sorted_noalloc,
     lib,
     library_path,
     moments,

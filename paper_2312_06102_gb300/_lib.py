@@ -86,6 +86,8 @@ def lib():
         L.tb_stage_name.restype = C.c_char_p
         L.tb_sort_variant.argtypes = [C.c_int32, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
         L.tb_sort_variant.restype = C.c_int32
+        L.tb_keys_sorted_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, P(C.c_double), _vp]
+        L.tb_keys_sorted_noalloc.restype = C.c_int
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
         L.tb_selftest_wait.restype = C.c_int
         _lib = L
@@ -275,6 +277,20 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
                                   _stream(stream), C.byref(t._p))
     _check(code, "tb_build_batched")
     return t
+
+
+NOALLOC_MAX_N = 524288
+
+
+def keys_sorted_noalloc(pos: torch.Tensor, pkey_out: torch.Tensor, perm_out: torch.Tensor,
+                        stream=None):
+    """tb_keys_sorted_noalloc: keys and stable sort into caller-owned outputs
+    (uint64 [n], int32 [n]) with no device allocation; returns (status, root
+    [lo x, lo y, lo z, side])."""
+    root = (C.c_double * 4)()
+    code = lib().tb_keys_sorted_noalloc(_ptr(pos), pos.shape[0], _ptr(pkey_out), _ptr(perm_out),
+                                        root, _stream(stream))
+    return int(code), [float(v) for v in root]
 
 
 def selftest_wait(spin_limit: int, stream=None) -> int:
