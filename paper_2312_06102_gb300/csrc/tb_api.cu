@@ -62,6 +62,7 @@ tb_status from_cuda(cudaError_t e) {
 }
 
 tb_status from_dev(uint32_t st) {
+    if (st & kErrInvalid) return TB_EINVAL;
     if (st & kErrNonFinite) return TB_ENONFINITE;
     if (st & kErrTimeout) return TB_ETIMEOUT;
     if (st & kErrOverflow) return TB_EOVERFLOW;
@@ -351,9 +352,87 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
 tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_t *d_set_offsets,
                            int32_t n_sets, int64_t n_total, const tb_params *params,
                            tb_stream stream, tb_tree **tree) {
-    (void)d_pos; (void)d_mass; (void)d_set_offsets; (void)n_sets; (void)n_total; (void)params;
-    (void)stream; (void)tree;
-    return TB_EINVAL;
+    if (!tree || !valid_params(params) || n_sets < 0 || n_total < 0 || n_total > 2147483647LL)
+        return TB_EINVAL;
+    if (n_sets > 0 && !d_set_offsets) return TB_EINVAL;
+    if (n_total > 0 && (!d_pos || (reinterpret_cast<uintptr_t>(d_pos) & 3u))) return TB_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_mass) & 3u) return TB_EINVAL;
+    if (*tree && (*tree)->n_sets == 0 && (*tree)->n_particles > 0) return TB_EINVAL;   // a single tree
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    TreeState *S = *tree ? state_of(*tree) : nullptr;
+    if (!S) {
+        S = new (std::nothrow) TreeState();
+        if (!S) return TB_ENOMEM;
+        std::memset(&S->pub, 0, sizeof(tb_tree));
+        S->pub.internal = &S->ws;
+        *tree = &S->pub;
+    }
+    tb_status st = ensure_fixed(*S);
+    if (st != TB_OK) return st;
+    Workspace &ws = S->ws;
+    tb_tree &t = S->pub;
+    S->params = *params;
+    ws.last_stream = s;
+    t.n_particles = n_total;
+    t.n_crit = params->n_crit;
+    t.n_sets = n_sets;
+    st = ensure_particles(*S, n_total, default_sort_cfg(8), false);
+    if (st != TB_OK) return st;
+    if (n_sets > ws.set_cap || !t.set_cell_offset) {
+        cudaDeviceSynchronize();
+        dev_free(ws.set_order); dev_free(ws.set_cnt); dev_free(ws.set_leaf_off); dev_free(ws.set_ctr);
+        dev_free(t.set_particle_offset); dev_free(t.set_cell_offset); dev_free(t.set_root);
+        const int64_t cap = n_sets > 0 ? n_sets : 1;
+        if (!dev_alloc(ws.set_order, cap) || !dev_alloc(ws.set_cnt, cap * kLevelFields) ||
+            !dev_alloc(ws.set_leaf_off, cap + 1) || !dev_alloc(ws.set_ctr, 4) ||
+            !dev_alloc(t.set_particle_offset, cap + 1) || !dev_alloc(t.set_cell_offset, cap + 1) ||
+            !dev_alloc(t.set_root, 4 * cap))
+            return TB_ENOMEM;
+        ws.set_cap = cap;
+    }
+    if (params->cell_capacity > 0) {
+        st = ensure_cells(*S, params->cell_capacity, params->mom_mode == TB_MOM_FP64);
+        if (st != TB_OK) return st;
+    }
+    cudaError_t e = cudaMemsetAsync(ws.info, 0, sizeof(DevInfo), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.set_ctr, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess && n_sets > 0)
+        e = cudaMemcpyAsync(t.set_particle_offset, d_set_offsets, sizeof(int64_t) * (n_sets + 1),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (n_sets == 0 || n_total == 0) {
+        // nothing to build: offsets of the (empty) sets are all zero
+        if (n_sets > 0) {
+            e = cudaMemsetAsync(t.set_cell_offset, 0, sizeof(int64_t) * (n_sets + 1), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t.set_root, 0, sizeof(double) * 4 * n_sets, s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        t.n_cells = t.n_leaves = 0;
+        t.max_depth = 0;
+        return TB_OK;
+    }
+    mark(ws, "start", s);
+    e = launch_set_check(t.set_particle_offset, n_sets, n_total, ws, s);
+    if (e == cudaSuccess)
+        e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit, t, ws,
+                           params->cell_capacity, 0, params->mom_mode, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (params->cell_capacity == 0) {
+        st = read_info(*S, s);
+        if (ws.h_info->status & kErrInvalid) return TB_EINVAL;
+        if (st != TB_OK) return st;
+        st = ensure_cells(*S, ws.h_info->n_cells > 0 ? ws.h_info->n_cells : 1,
+                          params->mom_mode == TB_MOM_FP64);
+        if (st != TB_OK) return st;
+    }
+    e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit, t, ws,
+                       params->cell_capacity, 1, params->mom_mode, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (params->cell_capacity == 0) {
+        st = read_info(*S, s);
+        if (st != TB_OK) return st;
+    }
+    return TB_OK;
 }
 
 void tb_free(tb_tree *tree) {
@@ -366,8 +445,7 @@ void tb_free(tb_tree *tree) {
     dev_free(ws.info); dev_free(ws.hist); dev_free(ws.bbox_part);
     if (ws.h_info) cudaFreeHost(ws.h_info);
     for (cudaEvent_t e : ws.ev) cudaEventDestroy(e);
-    dev_free(ws.set_order); dev_free(ws.set_level); dev_free(ws.set_ctr);
-    dev_free(ws.bkeys_a); dev_free(ws.bkeys_b); dev_free(ws.bperm_b);
+    dev_free(ws.set_order); dev_free(ws.set_cnt); dev_free(ws.set_leaf_off); dev_free(ws.set_ctr);
     dev_free(tree->set_particle_offset); dev_free(tree->set_cell_offset); dev_free(tree->set_root);
     delete S;
 }

@@ -1,0 +1,583 @@
+// tb_batched.cu -- many independent trees in one call (tb_build_batched).
+//
+// Thousands of particle sets of uneven size each get their own tree (own
+// root cube, keys, sort, cells and moments, exactly as tb_build + tb_moments
+// would give for the set alone), with a fixed number of launches whatever the
+// number of sets:
+//   set_order_kernel    : sets ordered largest first (work-queue order);
+//   batch_front_kernel  : persistent, one 1024-thread block per set taken from
+//                         an atomic work queue: root cube, keys, (x, y, z, m)
+//                         records and the digit histograms of every pass, then a
+//                         stable LSD radix sort of the set inside the block (its
+//                         tiles in order, so no look-back is needed), then the
+//                         set's cell and leaf counts per level;
+//   batch_scan_kernel   : cell and leaf offsets of every set (set order);
+//   batch_emit_kernel   : persistent, one block per set: every cell with its
+//                         links (the single-tree emission, tile after tile with
+//                         running counts), then the set's particles in key order;
+//   batch_moments_kernel: persistent, one block per set: moments level by level,
+//                         deepest first, with a block barrier between levels.
+// The paper builds disjoint subtrees on dynamically scheduled threads
+// (Sec. 2.3.3); here the unit of dynamic scheduling is a whole set.
+#include <cfloat>
+
+#include "tb_cells.cuh"
+#include "tb_moments.cuh"
+
+namespace tb {
+
+namespace {
+
+constexpr int kBThreads = 1024;               // front / emit blocks (one particle per thread per tile)
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBRadixBits = 8;
+constexpr int kBRadix = 1 << kBRadixBits;
+constexpr int kBPasses = (63 + kBRadixBits - 1) / kBRadixBits;
+constexpr int kBItems = 4;                    // keys per thread of a sort tile
+constexpr int kBTile = kBThreads * kBItems;
+constexpr int kBMomThreads = 256;
+constexpr int kBigLeafSerial = 1 << 20;       // leaves above this are summed in FP64
+
+struct SortShared {
+    uint64_t keys[kBTile];
+    int32_t vals[kBTile];
+    uint32_t warp_hist[kBWarps][kBRadix + 1];
+    uint32_t hist[kBPasses][kBRadix];
+    uint32_t run[kBRadix];
+    uint32_t tile_off[kBRadix + 1];
+    uint32_t cnt[kBRadix];
+};
+
+struct BatchArgs {
+    const float *pos;
+    const float *mass;
+    const int64_t *off;       // [S+1]
+    const int32_t *order;     // [S]
+    int32_t n_sets;
+    int32_t ncrit;
+    uint64_t *pkey;
+    int32_t *perm;
+    uint64_t *kalt;
+    int32_t *palt;
+    float4 *xm;
+    float4 *xs;
+    uint32_t *set_cnt;        // [S][kLevelFields]
+    int64_t *set_cell_off;    // [S+1]
+    int64_t *set_leaf_off;    // [S+1]
+    double *set_root;         // [S][4]
+    uint32_t *queue;          // [4] work-queue tickets
+    DevInfo *info;
+};
+
+__host__ __device__ inline size_t batch_front_smem(int ncrit) {
+    size_t a = sizeof(SortShared), b = lv_smem_bytes(ncrit);
+    return (a > b ? a : b);
+}
+
+// Sets in descending size classes (floor(log2 size)), ascending index within
+// a class: the largest sets are taken from the queues first.
+__global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int32_t S,
+                                                         int32_t *order, const DevInfo *info) {
+    if (info->status & kErrInvalid) return;
+    __shared__ uint32_t cls[34];
+    if (threadIdx.x < 34) cls[threadIdx.x] = 0;
+    __syncthreads();
+    auto klass = [&](int s) {
+        int64_t n = off[s + 1] - off[s];
+        return n <= 0 ? 0 : 1 + (63 - __clzll((unsigned long long)n));   // 0 .. 32
+    };
+    for (int s = threadIdx.x; s < S; s += blockDim.x) atomicAdd(&cls[klass(s)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int c = 33; c >= 0; --c) { uint32_t v = cls[c]; cls[c] = run; run += v; }
+    }
+    __syncthreads();
+    // stable within a class: one thread walks the sets in order
+    if (threadIdx.x == 0)
+        for (int s = 0; s < S; ++s) order[cls[klass(s)]++] = s;
+}
+
+__device__ __forceinline__ int take_set(uint32_t *ticket, int32_t S, int *s_q) {
+    if (threadIdx.x == 0) *s_q = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int q = *s_q;
+    __syncthreads();
+    return q < S ? q : -1;
+}
+
+// Block-wide min / max / non-finite reduction of one set's positions.
+__device__ void set_root_cube(const float *__restrict__ pos, int64_t o, int64_t ns, float *s_red,
+                              uint32_t *s_bad) {
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    uint32_t bad = 0;
+    for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const float x = pos[3 * i + a];
+            bad |= !(fabsf(x) <= FLT_MAX);
+            mn[a] = fminf(mn[a], x);
+            mx[a] = fmaxf(mx[a], x);
+        }
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], sh));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], sh));
+        }
+        bad |= __shfl_xor_sync(0xffffffffu, bad, sh);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) { s_red[warp * 6 + a] = mn[a]; s_red[warp * 6 + 3 + a] = mx[a]; }
+        if (bad) atomicOr(s_bad, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = s_red[threadIdx.x];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            v = (threadIdx.x < 3) ? fminf(v, s_red[w * 6 + threadIdx.x])
+                                  : fmaxf(v, s_red[w * 6 + threadIdx.x]);
+        s_red[threadIdx.x] = v;   // warp 0's slots hold the result
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) {
+    if (A.info->status & kErrInvalid) return;
+    extern __shared__ __align__(16) unsigned char raw[];
+    SortShared &sm = *reinterpret_cast<SortShared *>(raw);
+    __shared__ TileShared ts;
+    __shared__ float s_red[kBWarps * 6];
+    __shared__ uint32_t s_bad, s_tot[kLevelFields];
+    __shared__ float s_lo[3], s_shi, s_slo;
+    __shared__ double s_scale;
+    __shared__ bool s_exact;
+    __shared__ int s_q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        const int q = take_set(&A.queue[0], A.n_sets, &s_q);
+        if (q < 0) return;
+        const int set = A.order[q];
+        const int64_t o = A.off[set], ns = A.off[set + 1] - o;
+        if (ns <= 0) {
+            if (threadIdx.x < kLevelFields) A.set_cnt[(int64_t)set * kLevelFields + threadIdx.x] = 0;
+            if (threadIdx.x < 4) A.set_root[4 * (int64_t)set + threadIdx.x] = threadIdx.x == 3 ? 1.0 : 0.0;
+            continue;
+        }
+        // ---- root cube (Sec. 2.2), as in root_kernel
+        if (threadIdx.x == 0) s_bad = 0;
+        __syncthreads();
+        set_root_cube(A.pos, o, ns, s_red, &s_bad);
+        if (threadIdx.x == 0) {
+            double L = 0.0;
+            float amax = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                s_lo[a] = s_red[a];
+                const double e = __dsub_rn((double)s_red[3 + a], (double)s_red[a]);
+                if (e > L) L = e;
+                amax = fmaxf(amax, fmaxf(fabsf(s_red[a]), fabsf(s_red[3 + a])));
+            }
+            if (!(L > 0.0)) L = 1.0;
+            const double scale = __ddiv_rn(2097152.0, L);
+            s_scale = scale;
+            s_shi = (float)scale;
+            s_slo = (float)__dsub_rn(scale, (double)s_shi);
+            s_exact = !(scale < 1e30 && scale > 1e-30 && amax < 1e30f);
+            for (int a = 0; a < 3; ++a) A.set_root[4 * (int64_t)set + a] = (double)s_lo[a];
+            A.set_root[4 * (int64_t)set + 3] = L;
+            if (s_bad) atomicOr(&A.info->status, kErrNonFinite);
+        }
+        for (int i = threadIdx.x; i < kBPasses * kBRadix; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+        __syncthreads();
+        // ---- keys, records and every pass's digit histogram
+        {
+            const float lx = s_lo[0], ly = s_lo[1], lz = s_lo[2], shi = s_shi, slo = s_slo;
+            const double sc = s_scale;
+            const bool ex = s_exact;
+            const float m_eq = (float)(1.0 / (double)ns);
+            // unsorted keys go where pass 0 reads them: kBPasses is even, so the
+            // passes run pkey -> kalt -> ... -> pkey
+            for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x) {
+                const float x = A.pos[3 * i], y = A.pos[3 * i + 1], z = A.pos[3 * i + 2];
+                const uint64_t k = morton_key(quantise(x, lx, shi, slo, sc, ex),
+                                              quantise(y, ly, shi, slo, sc, ex),
+                                              quantise(z, lz, shi, slo, sc, ex));
+                A.pkey[i] = k;
+                A.xm[i] = make_float4(x, y, z, A.mass ? A.mass[i] : m_eq);
+                for (int p = 0; p < kBPasses; ++p)
+                    atomicAdd(&sm.hist[p][(k >> (p * kBRadixBits)) & (kBRadix - 1)], 1u);
+            }
+        }
+        __syncthreads();
+        // ---- stable LSD sort of the set, tiles in order
+        uint64_t *src = A.pkey, *dst = A.kalt;
+        int32_t *vsrc = A.perm, *vdst = A.palt;
+        for (int p = 0; p < kBPasses; ++p) {
+            const int shift = p * kBRadixBits;
+            if (threadIdx.x == 0) {
+                uint32_t r = 0;
+                for (int d = 0; d < kBRadix; ++d) { sm.run[d] = r; r += sm.hist[p][d]; }
+            }
+            for (int64_t tb = 0; tb < ns; tb += kBTile) {
+                const int valid = (int)min64(kBTile, ns - tb);
+                for (int i = threadIdx.x; i < kBWarps * (kBRadix + 1); i += blockDim.x)
+                    (&sm.warp_hist[0][0])[i] = 0;
+                __syncthreads();
+                uint64_t key[kBItems];
+                int32_t val[kBItems];
+                uint32_t rank[kBItems];
+                const int wbase = warp * 32 * kBItems;
+#pragma unroll
+                for (int i = 0; i < kBItems; ++i) {
+                    const int e = wbase + i * 32 + lane;
+                    if (e < valid) {
+                        key[i] = src[o + tb + e];
+                        val[i] = (p == 0) ? (int32_t)(o + tb + e) : vsrc[o + tb + e];
+                    } else {
+                        key[i] = 0;
+                        val[i] = 0;
+                    }
+                }
+                // stable warp ranking: ballot peer masks, leader-updated counters
+                const unsigned lt = lanemask_lt();
+                uint32_t oldc[kBItems], lr[kBItems];
+#pragma unroll
+                for (int i = 0; i < kBItems; ++i) {
+                    const int e = wbase + i * 32 + lane;
+                    const uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (kBRadix - 1))
+                                                   : (uint32_t)kBRadix;
+                    unsigned peers = 0xffffffffu;
+#pragma unroll
+                    for (int b = 0; b <= kBRadixBits; ++b) {
+                        const bool bit = (d >> b) & 1u;
+                        const unsigned v = __ballot_sync(0xffffffffu, bit);
+                        peers &= bit ? v : ~v;
+                    }
+                    const int leader = __ffs(peers) - 1;
+                    oldc[i] = (lane == leader) ? atomicAdd(&sm.warp_hist[warp][d], (uint32_t)__popc(peers)) : 0u;
+                    lr[i] = (uint32_t)leader | ((uint32_t)__popc(peers & lt) << 8);
+                }
+#pragma unroll
+                for (int i = 0; i < kBItems; ++i)
+                    rank[i] = __shfl_sync(0xffffffffu, oldc[i], lr[i] & 31u) + (lr[i] >> 8);
+                __syncthreads();
+                // warp offsets within each digit, tile digit counts
+                for (int d = threadIdx.x; d < kBRadix; d += blockDim.x) {
+                    uint32_t acc = 0;
+                    for (int w = 0; w < kBWarps; ++w) {
+                        const uint32_t c = sm.warp_hist[w][d];
+                        sm.warp_hist[w][d] = acc;
+                        acc += c;
+                    }
+                    sm.cnt[d] = acc;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint32_t r = 0;
+                    for (int d = 0; d < kBRadix; ++d) { sm.tile_off[d] = r; r += sm.cnt[d]; }
+                    sm.tile_off[kBRadix] = r;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < kBItems; ++i) {
+                    const int e = wbase + i * 32 + lane;
+                    if (e < valid) {
+                        const uint32_t d = (uint32_t)((key[i] >> shift) & (kBRadix - 1));
+                        const uint32_t ps = sm.tile_off[d] + sm.warp_hist[warp][d] + rank[i];
+                        sm.keys[ps] = key[i];
+                        sm.vals[ps] = val[i];
+                    }
+                }
+                __syncthreads();
+                for (int j = threadIdx.x; j < valid; j += blockDim.x) {
+                    const uint64_t k = sm.keys[j];
+                    const uint32_t d = (uint32_t)((k >> shift) & (kBRadix - 1));
+                    const int64_t to = o + sm.run[d] + (j - sm.tile_off[d]);
+                    dst[to] = k;
+                    vdst[to] = sm.vals[j];
+                }
+                __syncthreads();
+                for (int d = threadIdx.x; d < kBRadix; d += blockDim.x) sm.run[d] += sm.cnt[d];
+                __syncthreads();
+            }
+            uint64_t *t = src; src = dst; dst = t;
+            int32_t *u = vsrc; vsrc = vdst; vdst = u;
+        }
+        // ---- cells and leaves started per level (the set is its own tree)
+        if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] = 0;
+        __syncthreads();
+        for (int64_t s = o; s < o + ns; s += kLvTile) {
+            const int64_t e = min64(o + ns, s + kLvTile);
+            tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            if (threadIdx.x < kLevelFields) {
+                uint32_t c = 0;
+                for (int w = 0; w < kLvWarps; ++w) c += __popc(ts.mask[w][threadIdx.x]);
+                s_tot[threadIdx.x] += c;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < kLevelFields)
+            A.set_cnt[(int64_t)set * kLevelFields + threadIdx.x] = s_tot[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Cell and leaf offsets of the sets (in set order), totals and depth.
+__global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t cell_cap) {
+    if (A.info->status & kErrInvalid) return;
+    __shared__ int64_t s_c[1024], s_l[1024];
+    __shared__ int s_dmax;
+    const int S = A.n_sets;
+    const int per = (S + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(S, lo + per);
+    int64_t c = 0, l = 0;
+    int dmax = 0;
+    for (int s = lo; s < hi; ++s) {
+        const uint32_t *r = A.set_cnt + (int64_t)s * kLevelFields;
+        for (int d = 0; d < kLevels; ++d) {
+            c += r[d];
+            if (r[d]) dmax = max(dmax, d);
+        }
+        l += r[kLevels];
+    }
+    if (threadIdx.x == 0) s_dmax = 0;
+    s_c[threadIdx.x] = c;
+    s_l[threadIdx.x] = l;
+    __syncthreads();
+    atomicMax(&s_dmax, dmax);
+    if (threadIdx.x == 0) {
+        int64_t rc = 0, rl = 0;
+        for (int t = 0; t < 1024; ++t) {
+            const int64_t vc = s_c[t], vl = s_l[t];
+            s_c[t] = rc;
+            s_l[t] = rl;
+            rc += vc;
+            rl += vl;
+        }
+        A.set_cell_off[S] = rc;
+        A.set_leaf_off[S] = rl;
+        A.info->n_cells = rc;
+        A.info->n_leaves = (uint32_t)rl;
+        for (int d = 0; d < kLevels; ++d) A.info->level_offset[d] = 0;
+        A.info->level_offset[kLevels] = rc;
+        if (cell_cap > 0 && rc > cell_cap) A.info->status |= kErrOverflow;
+    }
+    __syncthreads();
+    int64_t rc = s_c[threadIdx.x], rl = s_l[threadIdx.x];
+    for (int s = lo; s < hi; ++s) {
+        A.set_cell_off[s] = rc;
+        A.set_leaf_off[s] = rl;
+        const uint32_t *r = A.set_cnt + (int64_t)s * kLevelFields;
+        for (int d = 0; d < kLevels; ++d) rc += r[d];
+        rl += r[kLevels];
+    }
+    if (threadIdx.x == 0) A.info->max_depth = s_dmax;
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, EmitOut out) {
+    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+    extern __shared__ __align__(16) unsigned char raw[];
+    __shared__ TileShared ts;
+    __shared__ uint32_t woff[kLvWarps][kLevelFields];
+    __shared__ uint32_t s_run[kLevelFields], s_lvl[kLevelFields];
+    __shared__ int s_q;
+    for (;;) {
+        const int q = take_set(&A.queue[1], A.n_sets, &s_q);
+        if (q < 0) return;
+        const int set = A.order[q];
+        const int64_t o = A.off[set], ns = A.off[set + 1] - o;
+        if (ns <= 0) continue;
+        const int64_t cell_base = A.set_cell_off[set], leaf_base = A.set_leaf_off[set];
+        if (threadIdx.x == 0) {
+            uint32_t r = 0;
+            for (int d = 0; d < kLevels; ++d) {
+                s_lvl[d] = r;
+                r += A.set_cnt[(int64_t)set * kLevelFields + d];
+            }
+            s_lvl[kLevels] = 0;
+        }
+        if (threadIdx.x < kLevelFields) s_run[threadIdx.x] = 0;
+        __syncthreads();
+        for (int64_t s = o; s < o + ns; s += kLvTile) {
+            const int64_t e = min64(o + ns, s + kLvTile);
+            const Front f = tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            if (threadIdx.x < kLevelFields) {
+                const int fld = threadIdx.x;
+                uint32_t run = 0;
+                for (int w = 0; w < kLvWarps; ++w) {
+                    woff[w][fld] = run;
+                    run += __popc(ts.mask[w][fld]);
+                }
+                ts.base[fld] = (uint32_t)(((fld < kLevels) ? cell_base : leaf_base) + s_lvl[fld] +
+                                          s_run[fld]);
+            }
+            __syncthreads();
+            if (f.k < e) {
+                const int warp = threadIdx.x >> 5;
+                const unsigned lt = lanemask_lt();
+                auto P = [&](int d) {
+                    return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
+                };
+                const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[f.k - (s - A.ncrit - 1)];
+                emit_particle(f, P, o, o + ns, K, out);
+            }
+            __syncthreads();
+            if (threadIdx.x < kLevelFields) {
+                uint32_t c = 0;
+                for (int w = 0; w < kLvWarps; ++w) c += __popc(ts.mask[w][threadIdx.x]);
+                s_run[threadIdx.x] += c;
+            }
+            __syncthreads();
+        }
+        // the set's particles in key order, for its moments
+        for (int64_t k = o + threadIdx.x; k < o + ns; k += blockDim.x) A.xs[k] = A.xm[A.perm[k]];
+        __syncthreads();
+    }
+}
+
+// FP64 sum of a leaf too long for the FP32 routes (more than 2^20 members).
+__device__ __noinline__ void leaf_sum_f64_serial(const MomOut &o, const float4 *xs, int64_t c,
+                                                 int64_t pf, int64_t pe, bool has64) {
+    const float4 r0 = xs[pf];
+    const float ref[3] = {r0.x, r0.y, r0.z};
+    float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+    AccD D;
+    D.init();
+    for (int64_t k = pf; k < pe; ++k) {
+        const float4 v = xs[k];
+        const float x[3] = {v.x, v.y, v.z};
+        double dx[3];
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(bb[a], x[a]);
+            bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            dx[a] = (double)x[a] - (double)ref[a];
+        }
+        D.add((double)v.w, dx);
+    }
+    finish_d(o, c, D, ref, bb, has64);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBMomThreads, 3)
+    batch_moments_kernel(BatchArgs A, TreeIn T, MomOut o) {
+    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+    __shared__ int64_t s_lvl[kLevels + 1];
+    __shared__ int s_q;
+    for (;;) {
+        const int q = take_set(&A.queue[2], A.n_sets, &s_q);
+        if (q < 0) return;
+        const int set = A.order[q];
+        const int64_t ns = A.off[set + 1] - A.off[set];
+        if (ns <= 0) continue;
+        if (threadIdx.x == 0) {
+            int64_t r = A.set_cell_off[set];
+            for (int d = 0; d < kLevels; ++d) {
+                s_lvl[d] = r;
+                r += A.set_cnt[(int64_t)set * kLevelFields + d];
+            }
+            s_lvl[kLevels] = r;
+        }
+        __syncthreads();
+        for (int d = kDepthMax; d >= 0; --d) {
+            for (int64_t c = s_lvl[d] + threadIdx.x; c < s_lvl[d + 1]; c += blockDim.x) {
+                if (T.child_first[c] >= 0) {
+                    combine_children<MODE>(T, o, c);
+                } else {
+                    const int64_t pf = T.pfirst[c], pe = T.pend[c];
+                    if (pe - pf > kBigLeafSerial) leaf_sum_f64_serial(o, A.xs, c, pf, pe, MODE == TB_MOM_FP64);
+                    else leaf_sum<MODE>(o, A.xs, c, pf, pe);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The set offsets must partition [0, n_total): off[0] = 0, off[S] = n_total,
+// non-decreasing.  Otherwise every batched kernel skips its work.
+__global__ void set_check_kernel(const int64_t *off, int32_t S, int64_t n_total, DevInfo *info) {
+    bool bad = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bad = (off[0] != 0 || off[S] != n_total);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
+         s += (int64_t)gridDim.x * blockDim.x)
+        bad |= off[s + 1] < off[s] || off[s + 1] - off[s] > 2147483647LL;
+    if (bad) atomicOr(&info->status, kErrInvalid);
+}
+
+}  // namespace
+
+size_t batch_front_smem_bytes(int ncrit) { return batch_front_smem(ncrit); }
+
+cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Workspace &ws,
+                             cudaStream_t s) {
+    int grid = (S + 255) / 256;
+    if (grid < 1) grid = 1;
+    if (grid > 1024) grid = 1024;
+    set_check_kernel<<<grid, 256, 0, s>>>(off, S, n_total, ws.info);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *off, int32_t S,
+                           int ncrit, tb_tree &t, Workspace &ws, int64_t cell_cap, int phase,
+                           int mode, cudaStream_t s) {
+    BatchArgs A{pos, mass, off, ws.set_order, S, ncrit, t.pkey, t.perm, ws.keys_alt,
+                ws.perm_alt, ws.xm, ws.xs, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
+                t.set_root, ws.set_ctr, ws.info};
+    cudaError_t e;
+    static bool attr = false;
+    if (!attr) {
+        const int sm_front = (int)batch_front_smem(kMaxNcrit);
+        cudaFuncSetAttribute(batch_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_front);
+        cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lv_smem_bytes(kMaxNcrit));
+        cudaFuncSetAttribute(batch_front_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid_big = S < nsm ? (S > 0 ? S : 1) : nsm;
+    if (phase == 0) {
+        set_order_kernel<<<1, 1024, 0, s>>>(off, S, ws.set_order, ws.info);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        batch_front_kernel<<<grid_big, kBThreads, batch_front_smem(ncrit), s>>>(A);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        mark(ws, "batch_front", s);
+        batch_scan_kernel<<<1, 1024, 0, s>>>(A, cell_cap);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        mark(ws, "batch_scan", s);
+        return cudaSuccess;
+    }
+    EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
+                t.leaf_cell};
+    batch_emit_kernel<<<grid_big, kBThreads, lv_smem_bytes(ncrit), s>>>(A, out);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(ws, "batch_emit", s);
+    TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+    MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
+    const int grid_mom = S < 3 * nsm ? (S > 0 ? S : 1) : 3 * nsm;
+    switch (mode) {
+        case TB_MOM_FP32_COMP:
+            batch_moments_kernel<TB_MOM_FP32_COMP><<<grid_mom, kBMomThreads, 0, s>>>(A, T, o);
+            break;
+        case TB_MOM_FP32_PLAIN:
+            batch_moments_kernel<TB_MOM_FP32_PLAIN><<<grid_mom, kBMomThreads, 0, s>>>(A, T, o);
+            break;
+        default:
+            batch_moments_kernel<TB_MOM_FP64><<<grid_mom, kBMomThreads, 0, s>>>(A, T, o);
+            break;
+    }
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(ws, "batch_moments", s);
+    return cudaSuccess;
+}
+
+}  // namespace tb

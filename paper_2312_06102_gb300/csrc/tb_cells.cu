@@ -37,99 +37,11 @@
 // L_k, a maximum over a window of n + 1 values of c, comes from a doubling
 // table: M_1 = c, M_2q[i] = max(M_q[i], M_q[i+q]); with p the largest power of
 // two <= n + 1, L_k = max(M_p[k-n], M_p[k-p+1]).
-#include "tb_device.cuh"
+#include "tb_cells.cuh"
 
 namespace tb {
 
 namespace {
-
-constexpr int kLvThreads = 1024;
-constexpr int kLvWarps = kLvThreads / 32;
-constexpr int kLvTile = kLvThreads;   // one particle per thread
-
-__host__ __device__ inline int lv_pow2(int ncrit) {
-    int p = 1;
-    while (2 * p <= ncrit + 1) p *= 2;
-    return p;
-}
-
-__host__ __device__ inline size_t lv_smem_bytes(int ncrit) {
-    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;   // keys of [s-n-1, e+n)
-    size_t nc = (size_t)kLvTile + ncrit + 1;                // c over [s-n-1, e)
-    return ((ext * 8 + 15) & ~size_t(15)) + 2 * ((nc + 15) & ~size_t(15)) + 64;
-}
-
-struct Front {
-    int m, L, Lprev;      // this thread's particle k (m = 255 beyond the tile)
-    int64_t k;
-};
-
-// Shared state of one tile: masks and counts per warp and field
-// (fields 0..21 = cell starts per level, 22 = leaf starts).
-struct TileShared {
-    uint32_t mask[kLvWarps][kLevelFields];
-    uint32_t base[kLevelFields];
-};
-
-// m, L and L of the previous particle for particle s + threadIdx.x, and the
-// ballot masks of the level starts of every warp.
-__device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t n, int ncrit, int64_t s,
-                            int64_t e, unsigned char *raw, TileShared &ts) {
-    const int64_t lo = s - ncrit - 1;
-    const int next = (int)(e + ncrit - lo);
-    const int nc = (int)(e - lo);
-    const size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
-    const size_t ncp = ((size_t)kLvTile + ncrit + 1 + 15) & ~size_t(15);
-    uint64_t *key = reinterpret_cast<uint64_t *>(raw);
-    uint8_t *A = raw + ((ext * 8 + 15) & ~size_t(15));
-    uint8_t *B = A + ncp;
-    for (int x = threadIdx.x; x < next; x += blockDim.x) {
-        const int64_t i = lo + x;
-        key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < nc; x += blockDim.x) {
-        const int64_t i = lo + x;
-        int v = 0;
-        if (i >= 0 && i + ncrit < n) v = min(kDepthMax, min_depth(key[x], key[x + ncrit]));
-        A[x] = (uint8_t)v;
-    }
-    __syncthreads();
-    const int p = lv_pow2(ncrit);
-    for (int q = 1; q < p; q *= 2) {
-        for (int x = threadIdx.x; x < nc; x += blockDim.x)
-            B[x] = (x + q < nc) ? max(A[x], A[x + q]) : A[x];
-        __syncthreads();
-        uint8_t *t = A; A = B; B = t;
-    }
-    // A[x] = max of c over [x, x + p) (truncated at the end)
-    Front f;
-    f.k = s + threadIdx.x;
-    auto window = [&](int64_t k) {   // max c over [k - n, k], k in [s - 1, e)
-        const int x0 = (int)(k - ncrit - lo), x1 = (int)(k - p + 1 - lo);
-        return (int)max(A[x0], A[x1]);
-    };
-    if (f.k < e) {
-        const int x = (int)(f.k - lo);
-        f.m = (f.k == 0) ? 0 : min_depth(key[x - 1], key[x]);
-        f.L = window(f.k);
-        f.Lprev = window(f.k - 1);
-    } else {
-        f.m = 255;
-        f.L = 0;
-        f.Lprev = 0;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 0; d < kLevels; ++d) {
-        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
-        if (lane == 0) ts.mask[warp][d] = mk;
-    }
-    const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
-    if (lane == 0) ts.mask[warp][kLevels] = lm;
-    __syncthreads();
-    return f;
-}
 
 __global__ void __launch_bounds__(kLvThreads)
     level_count_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
@@ -138,7 +50,7 @@ __global__ void __launch_bounds__(kLvThreads)
     __shared__ TileShared ts;
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    tile_front(skeys, n, ncrit, s, e, raw, ts);
+    tile_front(skeys, 0, n, ncrit, s, e, raw, ts);
     if (threadIdx.x < kLevelFields) {
         uint32_t sum = 0;
         for (int w = 0; w < kLvWarps; ++w) sum += __popc(ts.mask[w][threadIdx.x]);
@@ -208,13 +120,6 @@ __global__ void __launch_bounds__(kScanThreads)
     info->misc_ctr[1] = 0;
 }
 
-struct EmitOut {
-    uint64_t *ckey;
-    uint8_t *level;
-    int32_t *parent, *child_first, *child_end, *pfirst, *pend;
-    int32_t *leaf_cell;
-};
-
 __global__ void __launch_bounds__(kLvThreads)
     emit_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
                 const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
@@ -225,7 +130,7 @@ __global__ void __launch_bounds__(kLvThreads)
     __shared__ uint32_t woff[kLvWarps][kLevelFields];
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    const Front f = tile_front(skeys, n, ncrit, s, e, raw, ts);
+    const Front f = tile_front(skeys, 0, n, ncrit, s, e, raw, ts);
     // exclusive prefix of the per-warp counts, and the tile's global base
     if (threadIdx.x < kLevelFields) {
         const int fld = threadIdx.x;
@@ -245,37 +150,8 @@ __global__ void __launch_bounds__(kLvThreads)
     auto P = [&](int d) {
         return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
     };
-    const int64_t k = f.k;
-    const int m = f.m, L = f.L;
-    if (k > 0) {
-        // close the cells holding k-1 but not k
-        for (int d = m; d <= f.Lprev; ++d) {
-            const uint32_t idx = P(d) - 1;
-            out.pend[idx] = (int32_t)k;
-            out.child_end[idx] = (d < f.Lprev) ? (int32_t)P(d + 1) : -1;
-        }
-    }
-    if (m <= L) {
-        const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[k - (s - ncrit - 1)];
-        for (int d = m; d <= L; ++d) {
-            const uint32_t idx = P(d);
-            out.ckey[idx] = cell_key(K, d);
-            out.level[idx] = (uint8_t)d;
-            out.pfirst[idx] = (int32_t)k;
-            out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == m ? 1 : 0);
-            out.child_first[idx] = (d < L) ? (int32_t)P(d + 1) : -1;
-        }
-        out.leaf_cell[P(kLevels)] = (int32_t)P(L);
-    }
-    if (k == n - 1) {
-        // the last particle closes every cell holding it
-        for (int d = 0; d <= L; ++d) {
-            const uint32_t own = (m <= d) ? 1u : 0u;
-            const uint32_t idx = P(d) + own - 1;
-            out.pend[idx] = (int32_t)n;
-            out.child_end[idx] = (d < L) ? (int32_t)(P(d + 1) + ((m <= d + 1) ? 1u : 0u)) : -1;
-        }
-    }
+    const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[f.k - (s - ncrit - 1)];
+    emit_particle(f, P, 0, n, K, out);
 }
 
 }  // namespace

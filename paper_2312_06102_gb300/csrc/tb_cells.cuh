@@ -1,0 +1,150 @@
+// tb_cells.cuh -- device code shared by the single-tree and the batched cell
+// emission: the per-tile derivation of m_k and L_k and of the per-level start
+// masks, and the cells one particle opens and closes.  See tb_cells.cu for
+// the method.
+#pragma once
+
+#include "tb_device.cuh"
+
+namespace tb {
+namespace {
+
+constexpr int kLvThreads = 1024;
+constexpr int kLvWarps = kLvThreads / 32;
+constexpr int kLvTile = kLvThreads;   // one particle per thread
+
+__host__ __device__ inline int lv_pow2(int ncrit) {
+    int p = 1;
+    while (2 * p <= ncrit + 1) p *= 2;
+    return p;
+}
+
+__host__ __device__ inline size_t lv_smem_bytes(int ncrit) {
+    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;   // keys of [s-n-1, e+n)
+    size_t nc = (size_t)kLvTile + ncrit + 1;                // c over [s-n-1, e)
+    return ((ext * 8 + 15) & ~size_t(15)) + 2 * ((nc + 15) & ~size_t(15)) + 64;
+}
+
+struct Front {
+    int m, L, Lprev;      // this thread's particle k (m = 255 beyond the tile)
+    int64_t k;
+};
+
+// Shared state of one tile: masks and counts per warp and field
+// (fields 0..21 = cell starts per level, 22 = leaf starts).
+struct TileShared {
+    uint32_t mask[kLvWarps][kLevelFields];
+    uint32_t base[kLevelFields];
+};
+
+// m, L and L of the previous particle for particle s + threadIdx.x of the
+// tile [s, e), and the ballot masks of the level starts of every warp.  The
+// tile lies in the segment [seg_lo, seg_hi) of sorted keys that forms one
+// tree (the whole array, or one set of a batch); keys outside it do not
+// exist for this tree.
+__device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, int64_t seg_hi,
+                            int ncrit, int64_t s, int64_t e, unsigned char *raw, TileShared &ts) {
+    const int64_t lo = s - ncrit - 1;
+    const int next = (int)(e + ncrit - lo);
+    const int nc = (int)(e - lo);
+    const size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
+    const size_t ncp = ((size_t)kLvTile + ncrit + 1 + 15) & ~size_t(15);
+    uint64_t *key = reinterpret_cast<uint64_t *>(raw);
+    uint8_t *A = raw + ((ext * 8 + 15) & ~size_t(15));
+    uint8_t *B = A + ncp;
+    for (int x = threadIdx.x; x < next; x += blockDim.x) {
+        const int64_t i = lo + x;
+        key[x] = (i >= seg_lo && i < seg_hi) ? skeys[i] : 0ull;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < nc; x += blockDim.x) {
+        const int64_t i = lo + x;
+        int v = 0;
+        if (i >= seg_lo && i + ncrit < seg_hi) v = min(kDepthMax, min_depth(key[x], key[x + ncrit]));
+        A[x] = (uint8_t)v;
+    }
+    __syncthreads();
+    const int p = lv_pow2(ncrit);
+    for (int q = 1; q < p; q *= 2) {
+        for (int x = threadIdx.x; x < nc; x += blockDim.x)
+            B[x] = (x + q < nc) ? max(A[x], A[x + q]) : A[x];
+        __syncthreads();
+        uint8_t *t = A; A = B; B = t;
+    }
+    // A[x] = max of c over [x, x + p) (truncated at the end)
+    Front f;
+    f.k = s + threadIdx.x;
+    auto window = [&](int64_t k) {   // max c over [k - n, k], k in [s - 1, e)
+        const int x0 = (int)(k - ncrit - lo), x1 = (int)(k - p + 1 - lo);
+        return (int)max(A[x0], A[x1]);
+    };
+    if (f.k < e) {
+        const int x = (int)(f.k - lo);
+        f.m = (f.k == seg_lo) ? 0 : min_depth(key[x - 1], key[x]);
+        f.L = window(f.k);
+        f.Lprev = window(f.k - 1);
+    } else {
+        f.m = 255;
+        f.L = 0;
+        f.Lprev = 0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < kLevels; ++d) {
+        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
+        if (lane == 0) ts.mask[warp][d] = mk;
+    }
+    const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
+    if (lane == 0) ts.mask[warp][kLevels] = lm;
+    __syncthreads();
+    return f;
+}
+
+
+struct EmitOut {
+    uint64_t *ckey;
+    uint8_t *level;
+    int32_t *parent, *child_first, *child_end, *pfirst, *pend;
+    int32_t *leaf_cell;
+};
+
+// Cells opened and closed by one particle.  P(d) is the global index of the
+// next level-d cell before k's own starts (P(kLevels): next leaf slot);
+// seg_hi is one past the tree's last particle; K is k's key.
+template <class PF>
+__device__ __forceinline__ void emit_particle(const Front &f, const PF &P, int64_t seg_lo,
+                                              int64_t seg_hi, uint64_t K, const EmitOut &out) {
+    const int64_t k = f.k;
+    const int m = f.m, L = f.L;
+    if (k > seg_lo) {
+        // close the cells holding k-1 but not k
+        for (int d = m; d <= f.Lprev; ++d) {
+            const uint32_t idx = P(d) - 1;
+            out.pend[idx] = (int32_t)k;
+            out.child_end[idx] = (d < f.Lprev) ? (int32_t)P(d + 1) : -1;
+        }
+    }
+    if (m <= L) {
+        for (int d = m; d <= L; ++d) {
+            const uint32_t idx = P(d);
+            out.ckey[idx] = cell_key(K, d);
+            out.level[idx] = (uint8_t)d;
+            out.pfirst[idx] = (int32_t)k;
+            out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == m ? 1 : 0);
+            out.child_first[idx] = (d < L) ? (int32_t)P(d + 1) : -1;
+        }
+        out.leaf_cell[P(kLevels)] = (int32_t)P(L);
+    }
+    if (k == seg_hi - 1) {
+        // the tree's last particle closes every cell holding it
+        for (int d = 0; d <= L; ++d) {
+            const uint32_t own = (m <= d) ? 1u : 0u;
+            const uint32_t idx = P(d) + own - 1;
+            out.pend[idx] = (int32_t)seg_hi;
+            out.child_end[idx] = (d < L) ? (int32_t)(P(d + 1) + ((m <= d + 1) ? 1u : 0u)) : -1;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace tb

@@ -21,6 +21,7 @@ constexpr int64_t kBigCell = int64_t(1) << 20;   // cells above this are summed 
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrOverflow = 2u;
 constexpr uint32_t kErrTimeout = 4u;
+constexpr uint32_t kErrInvalid = 8u;    // batched: set offsets not a partition of [0, n)
 
 // Record of one build, in device memory; written by the kernels, read back
 // by the host after a synchronisation.
@@ -89,12 +90,9 @@ struct Workspace {
     // batched
     int64_t set_cap = 0;
     int32_t *set_order = nullptr;    // [S] processing order (largest first)
-    int64_t *set_level = nullptr;    // [S][kLevelFields] per-set counts
-    uint32_t *set_ctr = nullptr;     // work-queue counters
-    uint64_t *bkeys_a = nullptr;     // batched sort scratch
-    uint64_t *bkeys_b = nullptr;
-    int32_t *bperm_b = nullptr;
-    int64_t batched_n_cap = 0;
+    uint32_t *set_cnt = nullptr;     // [S][kLevelFields] cells per level and leaves of each set
+    int64_t *set_leaf_off = nullptr; // [S+1]
+    uint32_t *set_ctr = nullptr;     // [4] work-queue tickets
 
     cudaStream_t last_stream = nullptr;
 };
@@ -124,6 +122,12 @@ int64_t bbox_grid();
 SortCfg default_sort_cfg(int radix_bits);
 const SortCfg *sort_variant(int i);
 bool sort_cfg_valid(const SortCfg &c);
+
+cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *off, int32_t S,
+                           int ncrit, tb_tree &t, Workspace &ws, int64_t cell_cap, int phase,
+                           int mode, cudaStream_t s);
+cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Workspace &ws,
+                             cudaStream_t s);
 
 void mark(Workspace &ws, const char *name, cudaStream_t s);
 

@@ -1,0 +1,145 @@
+"""tb_build_batched: every set is its own tree, identical to the oracle's tree
+of that set alone (structure bit-exact, moments within tolerance); indices
+in the batched output are global."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import batched_plummer, jitter_offsets, plummer, uniform_cube
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import TOL_COM, TOL_MASS, TOL_QUAD, tb, to_np, torch  # noqa: E402
+
+
+def _run(pos, mass, offsets, n_crit=16, cap=0, mode=0, tree=None):
+    m = tb()
+    p = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).cuda()
+    w = None if mass is None else torch.from_numpy(np.ascontiguousarray(mass, np.float32)).cuda()
+    off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
+    t = m.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, mom_mode=mode, tree=tree)
+    torch.cuda.synchronize()
+    assert t.sync() == 0
+    return t, p, w, off
+
+
+def _check_sets(t, pos, mass, offsets, n_crit, sets=None, mode=0):
+    offsets = np.asarray(offsets, np.int64)
+    S = len(offsets) - 1
+    g = {k: to_np(getattr(t, k)) for k in ("pkey", "perm", "ckey", "level", "parent",
+                                          "child_first", "child_end", "pfirst", "pend",
+                                          "mass", "com", "com_lo", "quad", "aabb")}
+    coff = to_np(t.set_cell_offset)
+    root = to_np(t.set_root)
+    assert coff[0] == 0 and coff[-1] == t.n_cells
+    for s in (range(S) if sets is None else sets):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        c0, c1 = int(coff[s]), int(coff[s + 1])
+        if b == a:
+            assert c1 == c0
+            continue
+        sp = pos[a:b]
+        sm = None if mass is None else mass[a:b]
+        o = oracle.build_tree(sp, n_crit)
+        assert c1 - c0 == o.n_cells, (s, c1 - c0, o.n_cells)
+        assert np.array_equal(g["pkey"][a:b], o.skeys), s
+        assert np.array_equal(g["perm"][a:b] - a, o.perm), s
+        sl = slice(c0, c1)
+        assert np.array_equal(g["ckey"][sl], o.ckey)
+        assert np.array_equal(g["level"][sl], o.level)
+        for k in ("pfirst", "pend"):
+            assert np.array_equal(g[k][sl] - a, getattr(o, k)), (s, k)
+        for k in ("parent", "child_first", "child_end"):
+            want = getattr(o, k).astype(np.int64)
+            want = np.where(want >= 0, want + c0, -1)
+            assert np.array_equal(g[k][sl].astype(np.int64), want), (s, k)
+        assert np.array_equal(root[s, :3], o.lo) and root[s, 3] == o.side
+        M, com, quad, aabb = oracle.moments(o, sp, sm)
+        side = o.side / np.exp2(o.level.astype(np.int64))
+        gc = g["com"][sl].astype(np.float64) + g["com_lo"][sl].astype(np.float64)
+        assert np.abs(g["mass"][sl] / M - 1).max() <= TOL_MASS
+        assert (np.abs(gc - com).max(1) / side).max() <= TOL_COM
+        assert (np.abs(g["quad"][sl] - quad).max(1) / (M * side * side)).max() <= TOL_QUAD
+        assert np.array_equal(g["aabb"][sl], aabb)
+
+
+def _sets(sizes, seed):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, n in enumerate(sizes):
+        kind = i % 3
+        if kind == 0:
+            parts.append(uniform_cube(n, seed + i)[0] if n else np.zeros((0, 3), np.float32))
+        elif kind == 1:
+            parts.append(plummer(n, seed + i, a=0.02 + 0.01 * (i % 5))[0] if n else np.zeros((0, 3), np.float32))
+        else:
+            parts.append(rng.integers(0, 4, (n, 3)).astype(np.float32))   # duplicates
+    pos = np.concatenate(parts) if parts else np.zeros((0, 3), np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    mass = (rng.random(pos.shape[0]) + 0.5).astype(np.float32)
+    return pos, mass, offsets
+
+
+@pytest.mark.parametrize("n_crit", [1, 8, 16])
+def test_batched_mixed_sizes(n_crit):
+    sizes = [0, 1, 2, 16, 17, 100, 4095, 4096, 4097, 9000, 0, 3, 20_000, 65_536, 5]
+    pos, mass, offsets = _sets(sizes, 10 + n_crit)
+    t, *_ = _run(pos, mass, offsets, n_crit=n_crit)
+    _check_sets(t, pos, mass, offsets, n_crit)
+
+
+def test_batched_null_mass_and_fp64_mode():
+    sizes = [300, 5000, 1, 12_345]
+    pos, _, offsets = _sets(sizes, 77)
+    t, *_ = _run(pos, None, offsets, mode=2)
+    _check_sets(t, pos, None, offsets, 16)
+
+
+def test_batched_plummer_sets_sampled():
+    """The batched workload's recipe with 512 sets; 40 sets checked in full."""
+    b = batched_plummer(n_sets=512, seed=4)
+    t, *_ = _run(b.pos, b.mass, b.offsets)
+    rng = np.random.default_rng(1)
+    _check_sets(t, b.pos, b.mass, b.offsets, 16, sets=sorted(rng.choice(512, 40, replace=False)))
+
+
+def test_batched_graph_replay_with_jitter():
+    """Capacity mode needs no host sync; captured in a CUDA graph and replayed
+    on jittered positions (steps 1 and 3), each matching the oracle."""
+    m = tb()
+    b = batched_plummer(n_sets=64, seed=4)
+    t, p, w, off = _run(b.pos, b.mass, b.offsets)
+    cap = int(t.n_cells * 1.2) + 64
+    m.build_batched(p, w, off, cell_capacity=cap, tree=t)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            m.build_batched(p, w, off, cell_capacity=cap, tree=t, stream=s)
+    for step in (1, 3):
+        jit = jitter_offsets(4, step, b.offsets, b.scale)
+        pj = (b.pos + jit).astype(np.float32)
+        p.copy_(torch.from_numpy(pj))
+        g.replay()
+        torch.cuda.synchronize()
+        assert t.sync() == 0
+        _check_sets(t, pj, b.mass, b.offsets, 16, sets=[0, 1, 17, 40, 63])
+
+
+def test_batched_invalid_offsets_rejected():
+    m = tb()
+    pos, mass, offsets = _sets([10, 20, 30], 5)
+    bad = offsets.copy()
+    bad[2] = 5          # not non-decreasing
+    p = torch.from_numpy(pos).cuda()
+    with pytest.raises(m.TbError) as ei:
+        m.build_batched(p, None, torch.from_numpy(bad).cuda())
+    assert ei.value.name == "TB_EINVAL"
+
+
+def test_batched_empty():
+    m = tb()
+    t = m.build_batched(torch.zeros((0, 3), dtype=torch.float32, device="cuda"), None,
+                        torch.zeros(4, dtype=torch.int64, device="cuda"))
+    assert t.n_cells == 0
