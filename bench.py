@@ -44,6 +44,8 @@ from synth import WORKLOADS, batched_plummer, workload  # noqa: E402
 # source is unchanged (see profiles/).
 NCU_TRAFFIC = {}
 
+METRIC = "tree-build Mparticles/s + HBM roofline %; batched vs plain on same GB300"
+
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
@@ -181,7 +183,7 @@ def run_reference(a):
     tot = sum(times)
     value = m * len(times) / tot / 1e6
     sample = f"first {m} of the {n} particles of {a.workload}, full FP64 build + direct-sum moments"
-    out = {"metric": "tree-build Mparticles/s", "value": round(value, 4), "unit": "Mparticles/s",
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "Mparticles/s",
            "impl": "reference", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -301,7 +303,7 @@ def run_ours(a):
     build_s = ms / a.steps / 1e3
     stage_ms = {k: round(v[0] / a.steps, 4) for k, v in agg.items()}
 
-    out = {"metric": "tree-build Mparticles/s", "value": round(value, 2),
+    out = {"metric": METRIC, "value": round(value, 2),
            "unit": "Mparticles/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": round(ms / a.steps, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+u64",
@@ -371,8 +373,133 @@ def traffic_n(dig):
     return 1
 
 
+_MASK64 = (1 << 64) - 1
+
+
+def _u64(v):
+    """A uint64 constant as the int64 with the same bits."""
+    v &= _MASK64
+    return v - (1 << 64) if v >= 1 << 63 else v
+
+
+def _srl(x, k):
+    """Logical right shift of int64 tensors holding uint64 bits."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def _splitmix(x):
+    """SplitMix64 finaliser on int64 tensors (two's-complement wraparound)."""
+    z = x + _u64(0x9E3779B97F4A7C15)
+    z = (z ^ _srl(z, 30)) * _u64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _u64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+class Jitter:
+    """Per-step positions x_t = fp32(x_0 + j_t) of the batched workload, made on
+    the GPU with the same counter-based definition as synth.jitter_offsets."""
+
+    def __init__(self, torch, b, seed, dev="cuda"):
+        sizes = np.diff(b.offsets)
+        self.dev = dev
+        self.torch = torch
+        self.base = torch.from_numpy(b.pos).to(dev)
+        self.set_id = torch.from_numpy(np.repeat(np.arange(len(sizes), dtype=np.int64), sizes)).to(dev)
+        self.local = torch.from_numpy((np.arange(int(b.offsets[-1]), dtype=np.int64)
+                                       - np.repeat(b.offsets[:-1], sizes))).to(dev)
+        self.amp = torch.from_numpy(np.repeat((1e-4 * b.scale).astype(np.float32), sizes)).to(dev)
+        self.h0 = int(_splitmix(torch.tensor([seed], dtype=torch.int64))[0])
+
+    def fill(self, step, out):
+        t = self.torch
+        h1 = _splitmix(t.tensor([self.h0 ^ step], dtype=t.int64, device=self.dev))
+        h2 = _splitmix(h1 ^ self.set_id)
+        for ax in range(3):
+            h3 = _splitmix(h2 ^ ((self.local << 2) | ax))
+            u = _srl(h3, 40).to(t.float32) * (2.0 ** -24)
+            out[:, ax] = self.base[:, ax] + (2.0 * u - 1.0) * self.amp
+
+
 def run_batched(a, tb, torch):
-    raise RuntimeError("batched build not available in this build")
+    """4096 independent Plummer sets: one tb_build_batched per step, captured in
+    a CUDA graph and replayed on jittered positions, against the plain loop of
+    one tb_build + tb_moments per set, both timed with CUDA events."""
+    spec = WORKLOADS["batched_4096"]
+    t0 = time.perf_counter()
+    b = batched_plummer(n_sets=spec["n_sets"], seed=spec["seed"])
+    log(f"[bench] generated batched_4096 ({int(b.offsets[-1])} particles) in {time.perf_counter() - t0:.1f}s")
+    n = int(b.offsets[-1])
+    S = len(b.offsets) - 1
+    n_crit = spec["n_crit"]
+    p = torch.from_numpy(b.pos).cuda()
+    w = torch.from_numpy(b.mass).cuda()
+    off = torch.from_numpy(b.offsets).cuda()
+    jit = Jitter(torch, b, spec["seed"])
+    tree = tb.build_batched(p, w, off, n_crit=n_crit)
+    cap = int(tree.n_cells * 1.1) + 1024
+    stream = torch.cuda.Stream()
+    g_build = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+        jit.fill(0, p)
+        stream.synchronize()
+        l0 = tb.kernel_launches()
+        with torch.cuda.graph(g_build, stream=stream):
+            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+        per_build = tb.kernel_launches() - l0
+    steps = a.batched_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g_build.replay()
+        for t_ in range(steps):
+            jit.fill(t_ + 1, p)
+            evs[t_][0].record(stream)
+            g_build.replay()
+            evs[t_][1].record(stream)
+        stream.synchronize()
+    st = tree.sync(stream)
+    if st != 0:
+        raise RuntimeError(f"batched replay failed: {tb.STATUS[st]}")
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    batched_ms = float(np.median(ms))
+
+    # plain loop: one tb_build + tb_moments per set, one tree rebuilt in place
+    sizes = np.diff(b.offsets)
+    plain = tb.build(p[: int(sizes[0])], w[: int(sizes[0])], n_crit=n_crit)
+    caps = 0
+    for s_ in range(S):
+        lo_, hi_ = int(b.offsets[s_]), int(b.offsets[s_ + 1])
+        caps = max(caps, 2 * (hi_ - lo_) + 64)
+    loops = 2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    tw = time.perf_counter()
+    e0.record()
+    for _ in range(loops):
+        for s_ in range(S):
+            lo_, hi_ = int(b.offsets[s_]), int(b.offsets[s_ + 1])
+            ps, ws_ = p[lo_:hi_], w[lo_:hi_]
+            tb.build(ps, ws_, n_crit=n_crit, cell_capacity=caps, tree=plain)
+            tb.moments(plain, ps, ws_)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - tw) / loops * 1e3
+    plain_ms = e0.elapsed_time(e1) / loops
+    if plain.sync() != 0:
+        raise RuntimeError("plain loop failed")
+    return {"workload": "batched_4096", "sets": S, "particles": n, "n_crit": n_crit,
+            "graph_replays": steps, "cell_capacity": cap,
+            "batched_ms_per_build": round(batched_ms, 4),
+            "batched_mparticles_s": round(n / batched_ms / 1e3, 1),
+            "plain_loop_ms_per_build": round(plain_ms, 3),
+            "plain_loop_wall_ms": round(wall, 1),
+            "plain_loop_mparticles_s": round(n / plain_ms / 1e3, 2),
+            "speedup_vs_plain": round(plain_ms / batched_ms, 1),
+            "kernels_per_batched_build": int(per_build),
+            "timing": "CUDA events around each graph replay (jitter kernel outside); plain loop: "
+                      "events around the whole loop of per-set calls, no host sync inside"}
 
 
 def main():
