@@ -88,7 +88,7 @@ void free_particles(TreeState &S) {
     t.pos_sorted = nullptr;
     ws.xm_pos = ws.xm_mass = nullptr;
     dev_free(t.leaf_cell); dev_free(ws.big_leaf);
-    dev_free(ws.level_cnt); dev_free(ws.lookback);
+    dev_free(ws.level_cnt); dev_free(ws.lookback); dev_free(ws.ml);
     ws.n_cap = 0;
     ws.tiles_cap = 0;
     ws.level_tiles_cap = 0;
@@ -122,7 +122,7 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         int64_t lb = need_lb > 0 ? need_lb : 1;
         if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
             !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) || !dev_alloc(ws.xs, cap) ||
-            !dev_alloc(ws.big_leaf, cap) ||
+            !dev_alloc(ws.big_leaf, cap) || !dev_alloc(ws.ml, cap) ||
             !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
             return TB_ENOMEM;
         if (cudaMemset(ws.lookback, 0, sizeof(uint64_t) * lb) != cudaSuccess) return TB_ECUDA;

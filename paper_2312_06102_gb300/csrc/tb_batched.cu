@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
     SortShared &sm = *reinterpret_cast<SortShared *>(raw);
     __shared__ TileShared ts;
     __shared__ float s_red[kBWarps * 6];
-    __shared__ uint32_t s_bad, s_tot[kLevelFields];
+    __shared__ uint32_t s_bad, s_tot[kLevelFields], s_tile[kLevelFields];
     __shared__ float s_lo[3], s_shi, s_slo;
     __shared__ double s_scale;
     __shared__ bool s_exact;
@@ -308,11 +308,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
         for (int64_t s = o; s < o + ns; s += kLvTile) {
             const int64_t e = min64(o + ns, s + kLvTile);
             tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
-            if (threadIdx.x < kLevelFields) {
-                uint32_t c = 0;
-                for (int w = 0; w < kLvWarps; ++w) c += __popc(ts.mask[w][threadIdx.x]);
-                s_tot[threadIdx.x] += c;
-            }
+            warp_field_prefix(ts, nullptr, s_tile);
+            __syncthreads();
+            if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] += s_tile[threadIdx.x];
             __syncthreads();
         }
         if (threadIdx.x < kLevelFields)
@@ -378,7 +376,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, E
     extern __shared__ __align__(16) unsigned char raw[];
     __shared__ TileShared ts;
     __shared__ uint32_t woff[kLvWarps][kLevelFields];
-    __shared__ uint32_t s_run[kLevelFields], s_lvl[kLevelFields];
+    __shared__ uint32_t s_run[kLevelFields], s_lvl[kLevelFields], s_tile[kLevelFields];
     __shared__ int s_q;
     for (;;) {
         const int q = take_set(&A.queue[1], A.n_sets, &s_q);
@@ -400,13 +398,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, E
         for (int64_t s = o; s < o + ns; s += kLvTile) {
             const int64_t e = min64(o + ns, s + kLvTile);
             const Front f = tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            warp_field_prefix(ts, woff, s_tile);
             if (threadIdx.x < kLevelFields) {
                 const int fld = threadIdx.x;
-                uint32_t run = 0;
-                for (int w = 0; w < kLvWarps; ++w) {
-                    woff[w][fld] = run;
-                    run += __popc(ts.mask[w][fld]);
-                }
                 ts.base[fld] = (uint32_t)(((fld < kLevels) ? cell_base : leaf_base) + s_lvl[fld] +
                                           s_run[fld]);
             }
@@ -421,11 +415,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, E
                 emit_particle(f, P, o, o + ns, K, out);
             }
             __syncthreads();
-            if (threadIdx.x < kLevelFields) {
-                uint32_t c = 0;
-                for (int w = 0; w < kLvWarps; ++w) c += __popc(ts.mask[w][threadIdx.x]);
-                s_run[threadIdx.x] += c;
-            }
+            if (threadIdx.x < kLevelFields) s_run[threadIdx.x] += s_tile[threadIdx.x];
             __syncthreads();
         }
         // the set's particles in key order, for its moments

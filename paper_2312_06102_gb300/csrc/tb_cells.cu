@@ -45,17 +45,18 @@ namespace {
 
 __global__ void __launch_bounds__(kLvThreads)
     level_count_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
-                       uint32_t *__restrict__ tile_cnt, int64_t n_tiles) {
+                       uint32_t *__restrict__ tile_cnt, int64_t n_tiles, uint16_t *__restrict__ ml) {
     extern __shared__ __align__(16) unsigned char raw[];
     __shared__ TileShared ts;
+    __shared__ uint32_t tot[kLevelFields];
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    tile_front(skeys, 0, n, ncrit, s, e, raw, ts);
-    if (threadIdx.x < kLevelFields) {
-        uint32_t sum = 0;
-        for (int w = 0; w < kLvWarps; ++w) sum += __popc(ts.mask[w][threadIdx.x]);
-        tile_cnt[(int64_t)threadIdx.x * n_tiles + t] = sum;
-    }
+    const Front f = tile_front(skeys, 0, n, ncrit, s, e, raw, ts);
+    // keep m and L of every particle for the emission
+    if (f.k < e) ml[f.k] = (uint16_t)(f.m | (f.L << 8));
+    warp_field_prefix(ts, nullptr, tot);
+    __syncthreads();
+    if (threadIdx.x < kLevelFields) tile_cnt[(int64_t)threadIdx.x * n_tiles + t] = tot[threadIdx.x];
 }
 
 // One block per field: exclusive prefix over tiles (in place); the last block
@@ -121,36 +122,53 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 __global__ void __launch_bounds__(kLvThreads)
-    emit_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
+    emit_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
                 const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
                 EmitOut out) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    extern __shared__ __align__(16) unsigned char raw[];
     __shared__ TileShared ts;
     __shared__ uint32_t woff[kLvWarps][kLevelFields];
+    __shared__ uint32_t tot[kLevelFields];
+    __shared__ uint8_t s_L[kLvTile];
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    const Front f = tile_front(skeys, 0, n, ncrit, s, e, raw, ts);
-    // exclusive prefix of the per-warp counts, and the tile's global base
-    if (threadIdx.x < kLevelFields) {
-        const int fld = threadIdx.x;
-        uint32_t run = 0;
-        for (int w = 0; w < kLvWarps; ++w) {
-            woff[w][fld] = run;
-            run += __popc(ts.mask[w][fld]);
-        }
-        ts.base[fld] = ((fld < kLevels) ? (uint32_t)info->level_offset[fld] : 0u) +
-                       tile_off[(int64_t)fld * n_tiles + t];
+    // m and L from the count pass; L of the particle before from the
+    // neighbouring thread (or, for the tile's first, from memory)
+    Front f;
+    f.k = s + threadIdx.x;
+    if (f.k < e) {
+        const uint32_t v = ml[f.k];
+        f.m = v & 255u;
+        f.L = v >> 8;
+    } else {
+        f.m = 255;
+        f.L = 0;
+    }
+    s_L[threadIdx.x] = (uint8_t)f.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < kLevels; ++d) {
+        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
+        if (lane == d) ts.mask[warp][d] = mk;
+    }
+    {
+        const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
+        if (lane == kLevels) ts.mask[warp][kLevels] = lm;
     }
     __syncthreads();
+    warp_field_prefix(ts, woff, tot);
+    if (threadIdx.x < kLevelFields)
+        ts.base[threadIdx.x] = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
+                               tile_off[(int64_t)threadIdx.x * n_tiles + t];
+    f.Lprev = (threadIdx.x > 0) ? s_L[threadIdx.x - 1] : (f.k > 0 ? (ml[f.k - 1] >> 8) : 0);
+    __syncthreads();
     if (f.k >= e) return;
-    const int warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     // P_d(k): level-d starts before k, as a global cell index
     auto P = [&](int d) {
         return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
     };
-    const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[f.k - (s - ncrit - 1)];
+    const uint64_t K = (f.m <= f.L) ? skeys[f.k] : 0ull;
     emit_particle(f, P, 0, n, K, out);
 }
 
@@ -166,16 +184,12 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int ncrit, Workspace
     if (!attr) {
         cudaFuncSetAttribute(level_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lv_smem_bytes(kMaxNcrit));
-        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)lv_smem_bytes(kMaxNcrit));
         cudaFuncSetAttribute(level_count_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     level_count_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt,
-                                                                 tiles);
+                                                                 tiles, ws.ml);
     ++g_launches;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -187,12 +201,12 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int ncrit, Workspace
 
 cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int ncrit, Workspace &ws, tb_tree &t,
                         cudaStream_t s) {
+    (void)ncrit;
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
-    const size_t smem = lv_smem_bytes(ncrit);
     EmitOut o{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
               t.leaf_cell};
-    emit_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt, tiles,
-                                                          ws.info, o);
+    emit_kernel<<<(unsigned)tiles, kLvThreads, 0, s>>>(skeys, ws.ml, n, ws.level_cnt, tiles,
+                                                       ws.info, o);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -101,6 +101,26 @@ __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, 
 }
 
 
+// Per-field prefix over the 32 warps of a 1024-thread tile, one warp per
+// field (fields 0..22): woff[w][f] = starts of field f in warps before w;
+// tot[f] = the tile's total.  Needs a barrier before (masks written) and
+// after (results read).
+__device__ __forceinline__ void warp_field_prefix(const TileShared &ts,
+                                                  uint32_t (*woff)[kLevelFields], uint32_t *tot) {
+    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
+    if (f < kLevelFields) {
+        const uint32_t v = __popc(ts.mask[lane][f]);
+        uint32_t x = v;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, sh);
+            if (lane >= sh) x += y;
+        }
+        if (woff) woff[lane][f] = x - v;
+        if (lane == 31) tot[f] = x;
+    }
+}
+
 struct EmitOut {
     uint64_t *ckey;
     uint8_t *level;

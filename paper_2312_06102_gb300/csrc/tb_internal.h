@@ -75,6 +75,7 @@ struct Workspace {
     uint64_t *lookback = nullptr;    // [tiles][radix]
     float *bbox_part = nullptr;      // [blocks][8]
     uint32_t *level_cnt = nullptr;   // [level tiles][kLevelFields]
+    uint16_t *ml = nullptr;          // [n] m_k | L_k << 8 of each sorted particle
     int32_t *big_leaf = nullptr;     // [n] queue of depth-21 leaves too long for one thread
     DevInfo *info = nullptr;
     DevInfo *h_info = nullptr;       // pinned host mirror
