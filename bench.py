@@ -63,6 +63,7 @@ def args_():
     ap.add_argument("--n-crit", type=int, default=0)
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--sort-variant", default="", help="bits,threads,items of a compiled variant")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -225,7 +226,9 @@ def run_ours(a):
     # pick the radix-sort variant on this workload (untimed), unless one is named
     cfg = None
     tune_ms = None
-    if a.radix_bits:
+    if a.sort_variant:
+        cfg = tuple(int(v) for v in a.sort_variant.split(","))
+    elif a.radix_bits:
         cfg = next(v for v in tb.sort_variants() if v[0] == a.radix_bits)
     elif not a.no_autotune:
         from paper_2312_06102_gb300 import autotune

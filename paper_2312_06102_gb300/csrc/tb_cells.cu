@@ -132,18 +132,22 @@ __global__ void __launch_bounds__(kLvThreads)
     __shared__ uint8_t s_L[kLvTile];
     const int64_t t = blockIdx.x;
     const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    // m and L from the count pass; L of the particle before from the
-    // neighbouring thread (or, for the tile's first, from memory)
+    // every global load of the block is issued first, so that their
+    // latencies overlap: m and L from the count pass (and L of the particle
+    // before the tile), the key, and the tile's offsets
     Front f;
     f.k = s + threadIdx.x;
-    if (f.k < e) {
-        const uint32_t v = ml[f.k];
-        f.m = v & 255u;
-        f.L = v >> 8;
-    } else {
-        f.m = 255;
-        f.L = 0;
-    }
+    const bool in = f.k < e;
+    const uint32_t v = in ? (uint32_t)ml[f.k] : 255u;
+    const uint64_t Kpre = in ? skeys[f.k] : 0ull;
+    uint32_t Lbefore = 0;
+    if (threadIdx.x == 0 && f.k > 0) Lbefore = (uint32_t)(ml[f.k - 1] >> 8);
+    uint32_t base_v = 0;
+    if (threadIdx.x < kLevelFields)
+        base_v = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
+                 tile_off[(int64_t)threadIdx.x * n_tiles + t];
+    f.m = v & 255u;
+    f.L = in ? (int)(v >> 8) : 0;
     s_L[threadIdx.x] = (uint8_t)f.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -157,10 +161,8 @@ __global__ void __launch_bounds__(kLvThreads)
     }
     __syncthreads();
     warp_field_prefix(ts, woff, tot);
-    if (threadIdx.x < kLevelFields)
-        ts.base[threadIdx.x] = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
-                               tile_off[(int64_t)threadIdx.x * n_tiles + t];
-    f.Lprev = (threadIdx.x > 0) ? s_L[threadIdx.x - 1] : (f.k > 0 ? (ml[f.k - 1] >> 8) : 0);
+    if (threadIdx.x < kLevelFields) ts.base[threadIdx.x] = base_v;
+    f.Lprev = (threadIdx.x > 0) ? s_L[threadIdx.x - 1] : (int)Lbefore;
     __syncthreads();
     if (f.k >= e) return;
     const unsigned lt = lanemask_lt();
@@ -168,8 +170,7 @@ __global__ void __launch_bounds__(kLvThreads)
     auto P = [&](int d) {
         return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
     };
-    const uint64_t K = (f.m <= f.L) ? skeys[f.k] : 0ull;
-    emit_particle(f, P, 0, n, K, out);
+    emit_particle(f, P, 0, n, Kpre, out);
 }
 
 }  // namespace
