@@ -43,7 +43,7 @@ namespace tb {
 
 namespace {
 
-__global__ void __launch_bounds__(kLvThreads)
+__global__ void __launch_bounds__(kLvThreads, 2)
     level_count_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
                        uint32_t *__restrict__ tile_cnt, int64_t n_tiles, uint16_t *__restrict__ ml) {
     extern __shared__ __align__(16) unsigned char raw[];
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kScanThreads)
     info->misc_ctr[1] = 0;
 }
 
-__global__ void __launch_bounds__(kLvThreads)
+__global__ void __launch_bounds__(kLvThreads, 2)
     emit_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
                 const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
                 EmitOut out) {
@@ -149,16 +149,8 @@ __global__ void __launch_bounds__(kLvThreads)
     f.m = v & 255u;
     f.L = in ? (int)(v >> 8) : 0;
     s_L[threadIdx.x] = (uint8_t)f.L;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 0; d < kLevels; ++d) {
-        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
-        if (lane == d) ts.mask[warp][d] = mk;
-    }
-    {
-        const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
-        if (lane == kLevels) ts.mask[warp][kLevels] = lm;
-    }
+    const int warp = threadIdx.x >> 5;
+    store_level_masks(f.m, f.L, ts);
     __syncthreads();
     warp_field_prefix(ts, woff, tot);
     if (threadIdx.x < kLevelFields) ts.base[threadIdx.x] = base_v;

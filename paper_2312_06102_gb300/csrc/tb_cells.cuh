@@ -37,6 +37,23 @@ struct TileShared {
     uint32_t base[kLevelFields];
 };
 
+// Per-warp masks of the lanes starting a cell at each level (fields 0..21)
+// and of the lanes starting a leaf (field 22).  Each lane holds the interval
+// [m, L] as a row of bits; a 32 x 32 bit-matrix transpose across the warp
+// (five exchange rounds) leaves in lane d the mask of field d.
+__device__ __forceinline__ void store_level_masks(int m, int L, TileShared &ts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = (m <= L) ? (((2u << L) - (1u << m)) | (1u << kLevels)) : 0u;
+    uint32_t msk = 0x0000ffffu;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1, msk ^= msk << j) {
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        if (lane & j) x ^= ((y >> j) ^ x) & msk;
+        else x ^= (((x >> j) ^ y) & msk) << j;
+    }
+    if (lane < kLevelFields) ts.mask[warp][lane] = x;
+}
+
 // m, L and L of the previous particle for particle s + threadIdx.x of the
 // tile [s, e), and the ballot masks of the level starts of every warp.  The
 // tile lies in the segment [seg_lo, seg_hi) of sorted keys that forms one
@@ -88,14 +105,7 @@ __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, 
         f.L = 0;
         f.Lprev = 0;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 0; d < kLevels; ++d) {
-        const uint32_t mk = __ballot_sync(0xffffffffu, f.m <= d && d <= f.L);
-        if (lane == 0) ts.mask[warp][d] = mk;
-    }
-    const uint32_t lm = __ballot_sync(0xffffffffu, f.m <= f.L);
-    if (lane == 0) ts.mask[warp][kLevels] = lm;
+    store_level_masks(f.m, f.L, ts);
     __syncthreads();
     return f;
 }

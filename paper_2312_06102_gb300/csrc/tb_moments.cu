@@ -5,11 +5,13 @@
 //   gather_kernel        : particles in key order, (x, y, z, m) records
 //                          (Sec. 2.3 step 3, the reorder); every thread keeps
 //                          four independent gathers in flight;
-//   level_moments_kernel : one launch per level, deepest first: a leaf sums its
-//                          contiguous members, any other cell combines its
-//                          children, which the previous launch finished;
+//   leaf_moments_kernel  : every leaf sums its contiguous members (leaves in
+//                          key order, one launch for all levels);
 //   big_leaf_kernel      : depth-21 leaves of identical keys that are too long
-//                          for one thread, summed block-wide.
+//                          for one thread, summed block-wide;
+//   level_moments_kernel : one launch per level, deepest first: every other
+//                          cell combines its children, which earlier launches
+//                          finished.
 //
 // Moments of a cell: M = sum m; centre of mass c = sum m x / M; central
 // second moment Q = sum m (x - c)(x - c)^T (6 components xx xy xz yy yz zz);
@@ -56,30 +58,41 @@ __global__ void __launch_bounds__(256)
         xs[k] = __ldg(xm + perm[k]);
 }
 
-// Every cell of level d: leaves from their members, the others from their
-// children (finished by the launch for level d + 1).
+// Every leaf, in key order (so a warp reads one stretch of the records).
+// Leaves longer than kBigLeafThread -- only depth-21 leaves of identical keys
+// can be -- are queued for big_leaf_kernel.
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads, 3)
-    level_moments_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info, int d) {
+    leaf_moments_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell,
+                        const float4 *__restrict__ xs, DevInfo *info) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];
+    const int64_t nl = info->n_leaves;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += stride) {
-        if (T.child_first[c] >= 0) {
-            combine_children<MODE>(T, o, c);
-        } else {
-            const int64_t pf = T.pfirst[c], pe = T.pend[c];
-            if (d == kDepthMax && pe - pf > kBigLeafThread) {
-                uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
-                T.big_leaf[q] = (int32_t)c;
-                continue;
-            }
-            leaf_sum<MODE>(o, xs, c, pf, pe);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
+        const int64_t c = leaf_cell[j];
+        const int64_t pf = T.pfirst[c], pe = T.pend[c];
+        if (pe - pf > kBigLeafThread) {
+            const uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
+            T.big_leaf[q] = (int32_t)c;
+            continue;
         }
+        leaf_sum<MODE>(o, xs, c, pf, pe);
     }
 }
 
-// Block-wide sums of the long depth-21 leaves queued by the level-21 launch.
+// The non-leaf cells of level d, from their children (finished by the
+// launch for level d + 1, or by the leaf launches).
+template <int MODE>
+__global__ void __launch_bounds__(kMomThreads, 3)
+    level_moments_kernel(TreeIn T, MomOut o, DevInfo *info, int d) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += stride)
+        if (T.child_first[c] >= 0) combine_children<MODE>(T, o, c);
+}
+
+// Block-wide sums of the long depth-21 leaves queued by the leaf launch.
 template <int MODE>
 __global__ void __launch_bounds__(kBigThreads)
     big_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info) {
@@ -222,19 +235,21 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark(ws, "gather", s);
-    // one persistent grid per level; a level holds at most n cells
+    // one persistent grid per launch; a level holds at most n cells
     int64_t grid = (n + kMomThreads - 1) / kMomThreads;
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
-    for (int d = kDepthMax; d >= 0; --d) {
-        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xs, ws.info, d);
+    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs, ws.info);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xs, ws.info);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(ws, "leaves", s);
+    for (int d = kDepthMax - 1; d >= 0; --d) {
+        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.info, d);
         ++g_launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (d == kDepthMax) {
-            big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xs, ws.info);
-            ++g_launches;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
     }
     mark(ws, "moments", s);
     return cudaSuccess;
