@@ -69,6 +69,8 @@ def args_():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--precision", action="store_true",
+                    help="print the per-level moment error of the three modes against the oracle")
     return ap.parse_args()
 
 
@@ -507,10 +509,61 @@ def run_batched(a, tb, torch):
                       "events around the whole loop of per-set calls, no host sync inside"}
 
 
+def run_precision(a):
+    """Largest moment error per level for FP32-compensated, FP32-plain and FP64
+    moments against direct FP64 sums of the oracle (sampled cells)."""
+    import torch
+    import oracle
+    import paper_2312_06102_gb300 as tb
+    wl = a.workload if a.workload != "clustered_2p27" else "stress_2p26"
+    pos, mass, spec, n = gen(wl, a.n)
+    n_crit = a.n_crit or spec["n_crit"]
+    idx = oracle.PrefixIndex(pos)
+    p = torch.from_numpy(pos).cuda()
+    w = torch.from_numpy(mass).cuda()
+    rng = np.random.default_rng(0)
+    report = {"workload": wl, "n_particles": n, "n_crit": n_crit, "levels": {}}
+    cells = lv = None
+    for mode, name in ((0, "fp32_comp"), (1, "fp32_plain"), (2, "fp64")):
+        t = tb.build(p, w, n_crit=n_crit, mom_mode=mode)
+        tb.moments(t, p, w)
+        torch.cuda.synchronize()
+        if cells is None:
+            lv_all = t.level.cpu().numpy()
+            sel = []
+            for d in range(22):
+                ids = np.nonzero(lv_all == d)[0]
+                if len(ids):
+                    sel.append(ids if len(ids) <= 400 else rng.choice(ids, 400, replace=False))
+            cells = np.unique(np.concatenate(sel))
+            lv = lv_all[cells].astype(np.int64)
+            M, com, quad, aabb, cnt = idx.moments(mass, lv, t.ckey.cpu().numpy()[cells])
+        gm = t.mass.cpu().numpy()[cells].astype(np.float64)
+        gc = t.com.cpu().numpy()[cells].astype(np.float64) + t.com_lo.cpu().numpy()[cells].astype(np.float64)
+        gq = t.quad.cpu().numpy()[cells].astype(np.float64)
+        if mode == 2:
+            gm, gc, gq = (t.mass64.cpu().numpy()[cells], t.com64.cpu().numpy()[cells],
+                          t.quad64.cpu().numpy()[cells])
+        s = t.side / np.exp2(lv)
+        em = np.abs(gm / M - 1)
+        ec = np.abs(gc - com).max(1) / s
+        eq = np.abs(gq - quad).max(1) / (M * s * s)
+        for d in np.unique(lv):
+            r = report["levels"].setdefault(int(d), {"cells_sampled": int((lv == d).sum())})
+            k = lv == d
+            r[name] = {"mass_rel": float(em[k].max()), "com_per_side": float(ec[k].max()),
+                       "quad_per_Ms2": float(eq[k].max())}
+        t.free()
+    print(json.dumps(report), flush=True)
+    return 0
+
+
 def main():
     a = args_()
     if a.impl == "reference":
         return run_reference(a)
+    if a.precision:
+        return run_precision(a)
     return run_ours(a)
 
 

@@ -241,3 +241,48 @@ def tree_walk(tree: Tree, pos, mass, M, com, quad, targets, theta: float, eps: f
     lib().ora_tree_walk(tree._handle.h, _p(pos), _p(mass), _p(M), _p(com), _p(quad), theta, eps,
                         int(use_quad), _p(targets), targets.shape[0], _p(acc))
     return acc
+
+
+class PrefixIndex:
+    """The oracle's own key order (FP64 keys, stable sort) for locating the
+    members of a cell by its key prefix, on sizes where the full top-down
+    build is too slow for a test."""
+
+    def __init__(self, pos):
+        self.pos = _f32pos(pos)
+        self.keys, self.lo, self.side = keys(self.pos)
+        self.order = np.argsort(self.keys, kind="stable")
+        self.skeys = self.keys[self.order]
+
+    def members(self, level: int, ckey: int):
+        """Original indices of the particles whose key starts with ckey at depth level."""
+        sh = 63 - 3 * int(level)
+        lo_k = np.uint64(int(ckey) << sh)
+        hi_k = np.uint64((int(ckey) << sh) | ((1 << sh) - 1))
+        a = int(np.searchsorted(self.skeys, lo_k, side="left"))
+        b = int(np.searchsorted(self.skeys, hi_k, side="right"))
+        return self.order[a:b]
+
+    def moments(self, mass, levels, ckeys):
+        """Direct FP64 sums over each listed cell's members (Sec. 2.3 footnote):
+        (M, com[.,3], quad[.,6] central xx xy xz yy yz zz, aabb[.,6] f32, count)."""
+        n = len(levels)
+        M = np.empty(n)
+        com = np.empty((n, 3))
+        quad = np.empty((n, 6))
+        aabb = np.empty((n, 6), np.float32)
+        cnt = np.empty(n, np.int64)
+        m_eq = np.float64(np.float32(1.0 / max(1, self.pos.shape[0])))
+        for j, (lv, ck) in enumerate(zip(levels, ckeys)):
+            idx = self.members(lv, ck)
+            x = self.pos[idx].astype(np.float64)
+            m = np.full(len(idx), m_eq) if mass is None else mass[idx].astype(np.float64)
+            Mj = m.sum()
+            c = (m[:, None] * x).sum(0) / Mj if Mj != 0 else x[0].copy()
+            d = x - c
+            q = [(m * d[:, a] * d[:, b]).sum() for a, b in ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))]
+            M[j], com[j], quad[j] = Mj, c, q
+            aabb[j, :3] = self.pos[idx].min(0)
+            aabb[j, 3:] = self.pos[idx].max(0)
+            cnt[j] = len(idx)
+        return M, com, quad, aabb, cnt

@@ -71,15 +71,25 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2
     int32_t val[ITEMS];
     uint32_t rank[ITEMS];
     const int wbase = warp * 32 * ITEMS;
+    const bool full = valid == TILE;
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        int e = wbase + i * 32 + lane;
-        if (e < valid) {
+        for (int i = 0; i < ITEMS; ++i) {
+            const int e = wbase + i * 32 + lane;
             key[i] = keys_in[tile_base + e];
             val[i] = FIRST ? (int32_t)(tile_base + e) : vals_in[tile_base + e];
-        } else {
-            key[i] = 0;
-            val[i] = 0;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int e = wbase + i * 32 + lane;
+            if (e < valid) {
+                key[i] = keys_in[tile_base + e];
+                val[i] = FIRST ? (int32_t)(tile_base + e) : vals_in[tile_base + e];
+            } else {
+                key[i] = 0;
+                val[i] = 0;
+            }
         }
     }
 
@@ -92,13 +102,17 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2
     // order, which keeps equal digits in element order.
     const unsigned lt = lanemask_lt();
     uint32_t old_cnt[ITEMS], lead_rank[ITEMS];
+    // a full tile needs no sentinel bit: RADIX_BITS ballots per item
+    const int nbits = full ? RADIX_BITS : RADIX_BITS + 1;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const int e = wbase + i * 32 + lane;
-        const uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        const uint32_t d = (full || e < valid) ? (uint32_t)((key[i] >> shift) & (RADIX - 1))
+                                               : (uint32_t)RADIX;
         unsigned peers = 0xffffffffu;
 #pragma unroll
         for (int b = 0; b <= RADIX_BITS; ++b) {
+            if (b == RADIX_BITS && nbits == RADIX_BITS) break;
             const bool bit = (d >> b) & 1u;
             const unsigned v = __ballot_sync(0xffffffffu, bit);
             peers &= bit ? v : ~v;

@@ -435,3 +435,23 @@ def test_tree_walk_quadrupole_helps_and_error_grows_with_theta():
     assert np.median(e_quad) < 0.5 * np.median(e_mono)
     meds = [np.median(_forces(4096, th)) for th in (0.3, 0.6, 0.9)]
     assert meds[0] < meds[1] < meds[2]
+
+
+def test_prefix_index_moments_equal_tree_moments():
+    """The prefix-located direct sums agree with the top-down tree's direct
+    sums cell by cell (member sets and FP64 values)."""
+    pos, _ = clustered_halos(20_000, 17, n_halo=100)
+    rng = np.random.default_rng(17)
+    mass = (rng.random(20_000) + 0.1).astype(np.float32)
+    t = oracle.build_tree(pos, 8)
+    idx = oracle.PrefixIndex(pos)
+    assert np.array_equal(idx.skeys, t.skeys) and np.array_equal(idx.order, t.perm)
+    cells = np.arange(0, t.n_cells, max(1, t.n_cells // 300))
+    M, com, quad, aabb, cnt = idx.moments(mass, t.level[cells], t.ckey[cells])
+    M2, com2, quad2, aabb2 = oracle.moments(t, pos, mass, cells)
+    assert np.array_equal(cnt, (t.pend - t.pfirst)[cells])
+    assert np.allclose(M, M2, rtol=1e-13, atol=0)
+    s = t.side / np.exp2(t.level[cells].astype(np.int64))
+    assert (np.abs(com - com2).max(1) / s).max() < 1e-10
+    assert (np.abs(quad - quad2).max(1) / (M * s * s)).max() < 1e-9
+    assert np.array_equal(aabb, aabb2)
