@@ -105,17 +105,18 @@ def _gpu_arrays(t):
                                              "child_first", "child_end", "pfirst", "pend")}
 
 
-def _sample_cells(lv, leaf, rng, per_level=60):
-    cells = []
-    for d in range(22):
+def _sample_cells(lv, leaf, rng, per_level=60, extra_leaves=300):
+    """The root, a few cells of each shallow level (each holds a large share
+    of the particles, so its direct sum is costly), per_level random cells of
+    every deeper level, and random leaves."""
+    cells = [np.array([0])]
+    for d in range(1, 22):
         idx = np.nonzero(lv == d)[0]
         if len(idx) == 0:
             continue
-        if d <= 2:
-            cells.append(idx)
-        else:
-            cells.append(rng.choice(idx, min(per_level, len(idx)), replace=False))
-    extra = rng.choice(np.nonzero(leaf)[0], 300, replace=False)
+        k = 2 if d <= 2 else (per_level if d > 4 else per_level // 4)
+        cells.append(rng.choice(idx, min(k, len(idx)), replace=False))
+    extra = rng.choice(np.nonzero(leaf)[0], extra_leaves, replace=False)
     return np.unique(np.concatenate(cells + [extra]))
 
 
@@ -159,7 +160,8 @@ def test_clustered_2p27(n_crit):
     leaf = check_tree_properties(g, n, n_crit, idx.keys)
     assert np.allclose(t.lo, idx.lo, rtol=0, atol=0) and t.side == idx.side
     rng = np.random.default_rng(n_crit)
-    cells = _sample_cells(g["level"], leaf, rng, per_level=40 if n_crit != 16 else 80)
+    cells = _sample_cells(g["level"], leaf, rng, per_level=40 if n_crit != 16 else 80,
+                          extra_leaves=100 if n_crit != 16 else 300)
     em, ec, eq = _check_moments(t, g, idx, mass, cells)
     assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
 
