@@ -88,7 +88,7 @@ void free_particles(TreeState &S) {
     t.pos_sorted = nullptr;
     ws.xm_pos = ws.xm_mass = nullptr;
     dev_free(t.leaf_cell); dev_free(ws.big_leaf);
-    dev_free(ws.level_cnt); dev_free(ws.lookback); dev_free(ws.ml);
+    dev_free(ws.level_cnt); dev_free(ws.lookback); dev_free(ws.ml); dev_free(ws.long_runs);
     ws.n_cap = 0;
     ws.tiles_cap = 0;
     ws.level_tiles_cap = 0;
@@ -123,6 +123,7 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
             !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) || !dev_alloc(ws.xs, cap) ||
             !dev_alloc(ws.big_leaf, cap) || !dev_alloc(ws.ml, cap) ||
+            !dev_alloc(ws.long_runs, long_run_capacity(cap)) ||
             !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
             return TB_ENOMEM;
         if (cudaMemset(ws.lookback, 0, sizeof(uint64_t) * lb) != cudaSuccess) return TB_ECUDA;
@@ -287,7 +288,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
         st = ensure_cells(*S, params->cell_capacity, params->mom_mode == TB_MOM_FP64);
         if (st != TB_OK) return st;
     }
-    const int passes = sort_passes(cfg.radix_bits);
+    const int passes = sort_plan(cfg).passes;
     mark(ws, "start", s);
     cudaError_t e = launch_root(d_pos, n, ws, passes << cfg.radix_bits, s);
     if (e != cudaSuccess) return from_cuda(e);

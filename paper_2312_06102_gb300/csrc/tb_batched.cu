@@ -22,31 +22,22 @@
 #include <cfloat>
 
 #include "tb_cells.cuh"
+#include "tb_ctasort.cuh"
 #include "tb_moments.cuh"
 
 namespace tb {
 
 namespace {
 
-constexpr int kBThreads = 1024;               // front / emit blocks (one particle per thread per tile)
+constexpr int kBThreads = kCtaThreads;        // front / emit blocks (one particle per thread per tile)
 constexpr int kBWarps = kBThreads / 32;
-constexpr int kBRadixBits = 8;
-constexpr int kBRadix = 1 << kBRadixBits;
+constexpr int kBRadixBits = kCtaRadixBits;
+constexpr int kBRadix = kCtaRadix;
 constexpr int kBPasses = (63 + kBRadixBits - 1) / kBRadixBits;
-constexpr int kBItems = 4;                    // keys per thread of a sort tile
-constexpr int kBTile = kBThreads * kBItems;
 constexpr int kBMomThreads = 256;
 constexpr int kBigLeafSerial = 1 << 20;       // leaves above this are summed in FP64
 
-struct SortShared {
-    uint64_t keys[kBTile];
-    int32_t vals[kBTile];
-    uint32_t warp_hist[kBWarps][kBRadix + 1];
-    uint32_t hist[kBPasses][kBRadix];
-    uint32_t run[kBRadix];
-    uint32_t tile_off[kBRadix + 1];
-    uint32_t cnt[kBRadix];
-};
+using SortShared = CtaSortShared;
 
 struct BatchArgs {
     const float *pos;
@@ -152,7 +143,6 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
     __shared__ double s_scale;
     __shared__ bool s_exact;
     __shared__ int s_q;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         const int q = take_set(&A.queue[0], A.n_sets, &s_q);
         if (q < 0) return;
@@ -208,100 +198,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
             }
         }
         __syncthreads();
-        // ---- stable LSD sort of the set, tiles in order
-        uint64_t *src = A.pkey, *dst = A.kalt;
-        int32_t *vsrc = A.perm, *vdst = A.palt;
-        for (int p = 0; p < kBPasses; ++p) {
-            const int shift = p * kBRadixBits;
-            if (threadIdx.x == 0) {
-                uint32_t r = 0;
-                for (int d = 0; d < kBRadix; ++d) { sm.run[d] = r; r += sm.hist[p][d]; }
-            }
-            for (int64_t tb = 0; tb < ns; tb += kBTile) {
-                const int valid = (int)min64(kBTile, ns - tb);
-                for (int i = threadIdx.x; i < kBWarps * (kBRadix + 1); i += blockDim.x)
-                    (&sm.warp_hist[0][0])[i] = 0;
-                __syncthreads();
-                uint64_t key[kBItems];
-                int32_t val[kBItems];
-                uint32_t rank[kBItems];
-                const int wbase = warp * 32 * kBItems;
-#pragma unroll
-                for (int i = 0; i < kBItems; ++i) {
-                    const int e = wbase + i * 32 + lane;
-                    if (e < valid) {
-                        key[i] = src[o + tb + e];
-                        val[i] = (p == 0) ? (int32_t)(o + tb + e) : vsrc[o + tb + e];
-                    } else {
-                        key[i] = 0;
-                        val[i] = 0;
-                    }
-                }
-                // stable warp ranking: ballot peer masks, leader-updated counters
-                const unsigned lt = lanemask_lt();
-                uint32_t oldc[kBItems], lr[kBItems];
-#pragma unroll
-                for (int i = 0; i < kBItems; ++i) {
-                    const int e = wbase + i * 32 + lane;
-                    const uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (kBRadix - 1))
-                                                   : (uint32_t)kBRadix;
-                    unsigned peers = 0xffffffffu;
-#pragma unroll
-                    for (int b = 0; b <= kBRadixBits; ++b) {
-                        const bool bit = (d >> b) & 1u;
-                        const unsigned v = __ballot_sync(0xffffffffu, bit);
-                        peers &= bit ? v : ~v;
-                    }
-                    const int leader = __ffs(peers) - 1;
-                    oldc[i] = (lane == leader) ? atomicAdd(&sm.warp_hist[warp][d], (uint32_t)__popc(peers)) : 0u;
-                    lr[i] = (uint32_t)leader | ((uint32_t)__popc(peers & lt) << 8);
-                }
-#pragma unroll
-                for (int i = 0; i < kBItems; ++i)
-                    rank[i] = __shfl_sync(0xffffffffu, oldc[i], lr[i] & 31u) + (lr[i] >> 8);
-                __syncthreads();
-                // warp offsets within each digit, tile digit counts
-                for (int d = threadIdx.x; d < kBRadix; d += blockDim.x) {
-                    uint32_t acc = 0;
-                    for (int w = 0; w < kBWarps; ++w) {
-                        const uint32_t c = sm.warp_hist[w][d];
-                        sm.warp_hist[w][d] = acc;
-                        acc += c;
-                    }
-                    sm.cnt[d] = acc;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    uint32_t r = 0;
-                    for (int d = 0; d < kBRadix; ++d) { sm.tile_off[d] = r; r += sm.cnt[d]; }
-                    sm.tile_off[kBRadix] = r;
-                }
-                __syncthreads();
-#pragma unroll
-                for (int i = 0; i < kBItems; ++i) {
-                    const int e = wbase + i * 32 + lane;
-                    if (e < valid) {
-                        const uint32_t d = (uint32_t)((key[i] >> shift) & (kBRadix - 1));
-                        const uint32_t ps = sm.tile_off[d] + sm.warp_hist[warp][d] + rank[i];
-                        sm.keys[ps] = key[i];
-                        sm.vals[ps] = val[i];
-                    }
-                }
-                __syncthreads();
-                for (int j = threadIdx.x; j < valid; j += blockDim.x) {
-                    const uint64_t k = sm.keys[j];
-                    const uint32_t d = (uint32_t)((k >> shift) & (kBRadix - 1));
-                    const int64_t to = o + sm.run[d] + (j - sm.tile_off[d]);
-                    dst[to] = k;
-                    vdst[to] = sm.vals[j];
-                }
-                __syncthreads();
-                for (int d = threadIdx.x; d < kBRadix; d += blockDim.x) sm.run[d] += sm.cnt[d];
-                __syncthreads();
-            }
-            uint64_t *t = src; src = dst; dst = t;
-            int32_t *u = vsrc; vsrc = vdst; vdst = u;
-        }
+        // ---- stable LSD sort of the set (its digit counts were taken above)
+        cta_lsd_sort(A.pkey, A.perm, A.kalt, A.palt, o, ns, 0, kBPasses, true, sm);
+        __syncthreads();
         // ---- cells and leaves started per level (the set is its own tree)
         if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] = 0;
         __syncthreads();

@@ -1,0 +1,150 @@
+// tb_ctasort.cuh -- a stable LSD radix sort of one contiguous range of
+// (64-bit key, 32-bit value) pairs by a single 1024-thread block: every pass
+// takes the range's tiles in order with running per-digit offsets, so it
+// needs no coordination with other blocks.  Used for the sets of a batched
+// build and for the rare long runs left by the single-tree sort.
+#pragma once
+
+#include "tb_device.cuh"
+
+namespace tb {
+namespace {
+
+constexpr int kCtaThreads = 1024;
+constexpr int kCtaWarps = kCtaThreads / 32;
+constexpr int kCtaRadixBits = 8;
+constexpr int kCtaRadix = 1 << kCtaRadixBits;
+constexpr int kCtaMaxPasses = 8;
+constexpr int kCtaItems = 4;                     // keys per thread of a tile
+constexpr int kCtaTile = kCtaThreads * kCtaItems;
+
+struct CtaSortShared {
+    uint64_t keys[kCtaTile];
+    int32_t vals[kCtaTile];
+    uint32_t warp_hist[kCtaWarps][kCtaRadix + 1];
+    uint32_t hist[kCtaMaxPasses][kCtaRadix];
+    uint32_t run[kCtaRadix];
+    uint32_t tile_off[kCtaRadix + 1];
+    uint32_t cnt[kCtaRadix];
+};
+
+// Digit counts of every pass over [o, o + ns) into sm.hist.
+__device__ void cta_histograms(const uint64_t *keys, int64_t o, int64_t ns, int shift0, int passes,
+                               CtaSortShared &sm) {
+    for (int i = threadIdx.x; i < kCtaMaxPasses * kCtaRadix; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sm.hist[p][(k >> (shift0 + p * kCtaRadixBits)) & (kCtaRadix - 1)], 1u);
+    }
+    __syncthreads();
+}
+
+// Stable LSD sort of [o, o + ns) by the digits at shift0 + 8 p, p < passes,
+// with sm.hist holding each pass's digit counts.  Buffers alternate
+// (keys, vals) -> (alt_k, alt_v) -> ...; with index_vals the first pass takes
+// each element's own position as its value.  Returns the number of passes
+// (the result is in alt_k / alt_v when it is odd).
+__device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v,
+                            int64_t o, int64_t ns, int shift0, int passes, bool index_vals,
+                            CtaSortShared &sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *src = keys, *dst = alt_k;
+    int32_t *vsrc = vals, *vdst = alt_v;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = shift0 + p * kCtaRadixBits;
+        if (threadIdx.x == 0) {
+            uint32_t r = 0;
+            for (int d = 0; d < kCtaRadix; ++d) { sm.run[d] = r; r += sm.hist[p][d]; }
+        }
+        for (int64_t tb = 0; tb < ns; tb += kCtaTile) {
+            const int valid = (int)min64(kCtaTile, ns - tb);
+            for (int i = threadIdx.x; i < kCtaWarps * (kCtaRadix + 1); i += blockDim.x)
+                (&sm.warp_hist[0][0])[i] = 0;
+            __syncthreads();
+            uint64_t key[kCtaItems];
+            int32_t val[kCtaItems];
+            uint32_t rank[kCtaItems];
+            const int wbase = warp * 32 * kCtaItems;
+#pragma unroll
+            for (int i = 0; i < kCtaItems; ++i) {
+                const int e = wbase + i * 32 + lane;
+                if (e < valid) {
+                    key[i] = src[o + tb + e];
+                    val[i] = (p == 0 && index_vals) ? (int32_t)(o + tb + e) : vsrc[o + tb + e];
+                } else {
+                    key[i] = 0;
+                    val[i] = 0;
+                }
+            }
+            // stable warp ranking: ballot peer masks, leader-updated counters
+            const unsigned lt = lanemask_lt();
+            uint32_t oldc[kCtaItems], lr[kCtaItems];
+#pragma unroll
+            for (int i = 0; i < kCtaItems; ++i) {
+                const int e = wbase + i * 32 + lane;
+                const uint32_t d = (e < valid) ? (uint32_t)((key[i] >> shift) & (kCtaRadix - 1))
+                                               : (uint32_t)kCtaRadix;
+                unsigned peers = 0xffffffffu;
+#pragma unroll
+                for (int b = 0; b <= kCtaRadixBits; ++b) {
+                    const bool bit = (d >> b) & 1u;
+                    const unsigned v = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? v : ~v;
+                }
+                const int leader = __ffs(peers) - 1;
+                oldc[i] = (lane == leader) ? atomicAdd(&sm.warp_hist[warp][d], (uint32_t)__popc(peers)) : 0u;
+                lr[i] = (uint32_t)leader | ((uint32_t)__popc(peers & lt) << 8);
+            }
+#pragma unroll
+            for (int i = 0; i < kCtaItems; ++i)
+                rank[i] = __shfl_sync(0xffffffffu, oldc[i], lr[i] & 31u) + (lr[i] >> 8);
+            __syncthreads();
+            // warp offsets within each digit, tile digit counts
+            for (int d = threadIdx.x; d < kCtaRadix; d += blockDim.x) {
+                uint32_t acc = 0;
+                for (int w = 0; w < kCtaWarps; ++w) {
+                    const uint32_t c = sm.warp_hist[w][d];
+                    sm.warp_hist[w][d] = acc;
+                    acc += c;
+                }
+                sm.cnt[d] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t r = 0;
+                for (int d = 0; d < kCtaRadix; ++d) { sm.tile_off[d] = r; r += sm.cnt[d]; }
+                sm.tile_off[kCtaRadix] = r;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kCtaItems; ++i) {
+                const int e = wbase + i * 32 + lane;
+                if (e < valid) {
+                    const uint32_t d = (uint32_t)((key[i] >> shift) & (kCtaRadix - 1));
+                    const uint32_t ps = sm.tile_off[d] + sm.warp_hist[warp][d] + rank[i];
+                    sm.keys[ps] = key[i];
+                    sm.vals[ps] = val[i];
+                }
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < valid; j += blockDim.x) {
+                const uint64_t k = sm.keys[j];
+                const uint32_t d = (uint32_t)((k >> shift) & (kCtaRadix - 1));
+                const int64_t to = o + sm.run[d] + (j - sm.tile_off[d]);
+                dst[to] = k;
+                vdst[to] = sm.vals[j];
+            }
+            __syncthreads();
+            for (int d = threadIdx.x; d < kCtaRadix; d += blockDim.x) sm.run[d] += sm.cnt[d];
+            __syncthreads();
+        }
+        uint64_t *t = src; src = dst; dst = t;
+        int32_t *u = vsrc; vsrc = vdst; vdst = u;
+    }
+    return passes;
+}
+
+}  // namespace
+}  // namespace tb

@@ -41,7 +41,8 @@ struct DevInfo {
     int64_t level_offset[kLevels + 1];
     uint32_t sort_tile_ctr[16];   // dynamic tile ids, one counter per sort pass
     uint32_t misc_ctr[8];         // [0] bbox blocks done, [1] level-scan blocks done,
-                                  // [2] big-leaf queue length, [3] big-leaf tickets
+                                  // [2] big-leaf queue length, [3] big-leaf tickets,
+                                  // [4] key blocks done, [5] long sort runs, [6] their tickets
 };
 
 // Sort tuning: a compiled variant.
@@ -52,7 +53,14 @@ struct SortCfg {
     int tile() const { return threads * items; }
 };
 
-int sort_passes(int radix_bits);
+
+// Global radix passes of a variant and the lowest bit they sort from; the
+// runs of equal key >> shift0 are finished by the run step.
+struct SortPlan {
+    int passes;
+    int shift0;
+};
+SortPlan sort_plan(const SortCfg &c);
 
 // Workspace of one tree (device pointers unless noted).
 struct Workspace {
@@ -76,6 +84,7 @@ struct Workspace {
     float *bbox_part = nullptr;      // [blocks][8]
     uint32_t *level_cnt = nullptr;   // [level tiles][kLevelFields]
     uint16_t *ml = nullptr;          // [n] m_k | L_k << 8 of each sorted particle
+    int32_t *long_runs = nullptr;    // [n / 1024 + 2] sort runs too long for the run step
     int32_t *big_leaf = nullptr;     // [n] queue of depth-21 leaves too long for one thread
     DevInfo *info = nullptr;
     DevInfo *h_info = nullptr;       // pinned host mirror
@@ -129,6 +138,10 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                            int mode, cudaStream_t s);
 cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Workspace &ws,
                              cudaStream_t s);
+
+cudaError_t launch_runs(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v, int64_t n,
+                        int shift0, int32_t *long_runs, Workspace &ws, cudaStream_t s);
+int64_t long_run_capacity(int64_t n);
 
 void mark(Workspace &ws, const char *name, cudaStream_t s);
 

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restr
                                                             float m_eq, int64_t n, bool vec,
                                                             uint64_t *__restrict__ keys,
                                                             float4 *__restrict__ xm,
-                                                            uint32_t *hist, int passes,
+                                                            uint32_t *hist, int passes, int shift0,
                                                             DevInfo *info) {
     constexpr int RADIX = 1 << RADIX_BITS;
     extern __shared__ uint32_t s_hist[];   // [passes][RADIX]
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restr
 
     auto count = [&](uint64_t k) {
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&s_hist[p * RADIX + (int)((k >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);
+            atomicAdd(&s_hist[p * RADIX + (int)((k >> (shift0 + p * RADIX_BITS)) & (RADIX - 1))], 1u);
     };
     auto key_of = [&](float x, float y, float z) {
         return morton_key(quantise(x, lx, shi, slo, sc, exact), quantise(y, ly, shi, slo, sc, exact),
@@ -266,7 +266,7 @@ cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len
 
 template <int B>
 static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uint64_t *keys,
-                             Workspace &ws, int passes, cudaStream_t s) {
+                             Workspace &ws, int passes, int shift0, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(pos) & 15u) == 0 &&
                      (reinterpret_cast<uintptr_t>(mass) & 15u) == 0 &&
                      (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
@@ -281,19 +281,20 @@ static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uin
     int64_t need = (n + 4 * kKeysThreads - 1) / (4 * kKeysThreads);
     if (need < grid) grid = need < 1 ? 1 : need;
     keys_kernel<B><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, mass, m_eq, n, vec, keys, ws.xm,
-                                                              ws.hist, passes, ws.info);
+                                                              ws.hist, passes, shift0, ws.info);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
                         Workspace &ws, const SortCfg &cfg, cudaStream_t s) {
-    const int passes = sort_passes(cfg.radix_bits);
+    const SortPlan plan = sort_plan(cfg);
+    const int passes = plan.passes, shift0 = plan.shift0;
     switch (cfg.radix_bits) {
-        case 8: return keys_impl<8>(pos, mass, n, keys, ws, passes, s);
-        case 9: return keys_impl<9>(pos, mass, n, keys, ws, passes, s);
-        case 10: return keys_impl<10>(pos, mass, n, keys, ws, passes, s);
-        case 11: return keys_impl<11>(pos, mass, n, keys, ws, passes, s);
+        case 8: return keys_impl<8>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 9: return keys_impl<9>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 10: return keys_impl<10>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 11: return keys_impl<11>(pos, mass, n, keys, ws, passes, shift0, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -318,6 +319,5 @@ cudaError_t launch_pack(const float *pos, const float *mass, int64_t n, float4 *
     return cudaGetLastError();
 }
 
-int sort_passes(int radix_bits) { return (63 + radix_bits - 1) / radix_bits; }
 
 }  // namespace tb

@@ -7,8 +7,9 @@
 // code inside a latency-critical loop where cudaMalloc's implicit device
 // synchronisation is not acceptable, or code that must not grow its
 // footprint after start-up.  For them this file keeps the sort's scratch --
-// the digit histograms, the look-back array, the second key / index buffer
-// and the (x, y, z, m) records the key kernel writes -- in one file-scope
+// the digit histograms, the look-back array, the second key / index buffer,
+// the (x, y, z, m) records the key kernel writes and the queue of long sort
+// runs -- in one file-scope
 // device array of fixed size.  Every GPU that loads the library holds that
 // array (about 15 MB) until the process exits; particle counts above
 // TB_NOALLOC_MAX_N are refused.
@@ -43,7 +44,9 @@ constexpr size_t kLookWords = ((kNoAllocMaxN + 2047) / 2048) * (size_t(1) << kNo
 constexpr size_t kOffKeys = align256(kOffLook + sizeof(uint64_t) * kLookWords);
 constexpr size_t kOffPerm = align256(kOffKeys + sizeof(uint64_t) * kNoAllocMaxN);
 constexpr size_t kOffXm = align256(kOffPerm + sizeof(int32_t) * kNoAllocMaxN);
-constexpr size_t kScratchBytes = align256(kOffXm + 16 * size_t(kNoAllocMaxN));
+constexpr size_t kOffRuns = align256(kOffXm + 16 * size_t(kNoAllocMaxN));
+constexpr size_t kRunsCap = kNoAllocMaxN / 1024 + 2;   // long sort runs (> 1024 keys)
+constexpr size_t kScratchBytes = align256(kOffRuns + sizeof(int32_t) * kRunsCap);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -101,6 +104,8 @@ extern "C" tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint6
     ws.keys_alt = reinterpret_cast<uint64_t *>(base + kOffKeys);
     ws.perm_alt = reinterpret_cast<int32_t *>(base + kOffPerm);
     ws.xm = reinterpret_cast<float4 *>(base + kOffXm);
+    ws.long_runs = reinterpret_cast<int32_t *>(base + kOffRuns);
+    if (long_run_capacity(kNoAllocMaxN) > (int64_t)kRunsCap) return TB_ECUDA;
 
     // what must start at zero: the build record and its counters, and the
     // look-back words
@@ -115,7 +120,7 @@ extern "C" tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint6
         return status_of(cudaStreamSynchronize(s));
     }
     const SortCfg cfg = default_sort_cfg(kNoAllocRadixBits);
-    const int passes = sort_passes(cfg.radix_bits);
+    const int passes = sort_plan(cfg).passes;
     if ((e = launch_root(d_pos, n, ws, passes << cfg.radix_bits, s)) != cudaSuccess)
         return status_of(e);
     uint64_t *ka = (passes & 1) ? ws.keys_alt : d_pkey;

@@ -15,8 +15,10 @@
 //     hanging;
 //   - it orders the tile by digit in shared memory and writes keys and
 //     indices out as runs of consecutive addresses.
-// Digit offsets of every pass come from the histograms taken while the keys
-// were made.  Look-back words carry an epoch (build counter + pass) so that
+// The passes order the keys by their upper ceil(40 / b) * b bits only; the runs
+// of equal upper bits they leave (short in practice) are ordered by the low
+// bits afterwards (tb_runs.cu).  Digit offsets of every pass come from the
+// histograms taken while the keys were made.  Look-back words carry an epoch (build counter + pass) so that
 // the array is never cleared between passes or builds.
 #include "tb_device.cuh"
 
@@ -46,7 +48,7 @@ template <int RADIX_BITS, int THREADS, int ITEMS, bool FIRST>
 __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2) : (ITEMS <= 8 ? 2 : 1)))
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
-                    int pass, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
+                    int pass, int shift0, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
                     DevInfo *info, int64_t spin_limit) {
     using S = SortSmem<RADIX_BITS, THREADS, ITEMS>;
     constexpr int RADIX = S::RADIX;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2
     S &sm = *reinterpret_cast<S *>(smem_raw);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int shift = pass * RADIX_BITS;
+    const int shift = shift0 + pass * RADIX_BITS;
 
     if (threadIdx.x == 0) sm.tile = atomicAdd(&info->sort_tile_ctr[pass], 1u);
     for (int i = threadIdx.x; i < WARPS * (RADIX + 1); i += THREADS)
@@ -266,9 +268,9 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2
 
 template <int B, int T, int I>
 cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int64_t n,
-                       Workspace &ws, uint64_t *&kout, int32_t *&pout, cudaStream_t s) {
+                       Workspace &ws, const SortPlan &plan, uint64_t *&kout, int32_t *&pout,
+                       cudaStream_t s) {
     using S = SortSmem<B, T, I>;
-    const int passes = sort_passes(B);
     const size_t smem = sizeof(S);
     static bool attr = false;
     if (!attr) {
@@ -289,13 +291,15 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
     uint64_t *src = ka, *dst = kb;
     int32_t *vsrc = pa, *vdst = pb;
     const int64_t spin = int64_t(1) << 26;
-    for (int p = 0; p < passes; ++p) {
+    for (int p = 0; p < plan.passes; ++p) {
         if (p == 0)
             onesweep_kernel<B, T, I, true><<<(unsigned)tiles, T, smem, s>>>(
-                src, nullptr, dst, vdst, n, p, ws.hist + p * (1 << B), ws.lookback, ws.info, spin);
+                src, nullptr, dst, vdst, n, p, plan.shift0, ws.hist + p * (1 << B), ws.lookback,
+                ws.info, spin);
         else
             onesweep_kernel<B, T, I, false><<<(unsigned)tiles, T, smem, s>>>(
-                src, vsrc, dst, vdst, n, p, ws.hist + p * (1 << B), ws.lookback, ws.info, spin);
+                src, vsrc, dst, vdst, n, p, plan.shift0, ws.hist + p * (1 << B), ws.lookback,
+                ws.info, spin);
         ++g_launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -305,6 +309,10 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
     }
     kout = src;
     pout = vsrc;
+    // finish the runs of equal upper bits; the other buffers are free scratch
+    cudaError_t e = launch_runs(src, vsrc, dst, vdst, n, plan.shift0, ws.long_runs, ws, s);
+    if (e != cudaSuccess) return e;
+    if (plan.shift0 > 0) mark(ws, "sort_runs", s);
     return cudaSuccess;
 }
 
@@ -335,12 +343,21 @@ bool sort_cfg_valid(const SortCfg &c) {
 
 int64_t sort_tiles(const SortCfg &c, int64_t n) { return (n + c.tile() - 1) / c.tile(); }
 
+SortPlan sort_plan(const SortCfg &c) {
+    // global passes cover the upper ceil(40 / b) * b key bits; the runs of
+    // equal upper bits are finished locally
+    const int b = c.radix_bits;
+    const int passes = (40 + b - 1) / b;
+    return {passes, 63 - passes * b};
+}
+
 cudaError_t launch_sort(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int64_t n,
                         Workspace &ws, const SortCfg &cfg, uint64_t *&kout, int32_t *&pout,
                         cudaStream_t s) {
+    const SortPlan plan = sort_plan(cfg);
 #define TB_SORT_CASE(B, T, I)                                             \
     if (cfg.radix_bits == B && cfg.threads == T && cfg.items == I)        \
-        return run_passes<B, T, I>(ka, kb, pa, pb, n, ws, kout, pout, s);
+        return run_passes<B, T, I>(ka, kb, pa, pb, n, ws, plan, kout, pout, s);
     TB_SORT_CASE(8, 256, 16)
     TB_SORT_CASE(8, 512, 16)
     TB_SORT_CASE(8, 512, 12)

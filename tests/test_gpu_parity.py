@@ -88,6 +88,26 @@ def test_duplicates_and_identical():
     assert t.n_cells == 22
 
 
+@pytest.mark.parametrize("radix_bits", [8, 11])
+def test_long_sort_runs(radix_bits):
+    """Dense clusters inside single depth-13 cells: the keys share their upper
+    bits over runs of hundreds to thousands of particles (runs longer than the
+    run step's window go to the block sort), spread over tile boundaries."""
+    rng = np.random.default_rng(21)
+    parts = [rng.random((40_000, 3)), np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]])]
+    cell = 2.0 ** -13
+    for j, m in enumerate([300, 900, 1023, 1024, 1025, 1500, 2047, 2049, 5000, 12_000]):
+        corner = (np.array([3 + 7 * j, 5 + 11 * j, 2 + 13 * j]) + 0.2) * cell
+        parts.append(corner + rng.random((m, 3)) * (cell / 16))
+    pos = np.concatenate(parts).astype(np.float32)
+    pos = pos[rng.permutation(len(pos))]
+    mass = (rng.random(len(pos)) + 0.5).astype(np.float32)
+    t, o = _check(pos, mass, 16, radix_bits=radix_bits)
+    top = o.skeys >> np.uint64(63 - 40)
+    _, counts = np.unique(top, return_counts=True)
+    assert counts.max() > 4096
+
+
 def test_lattice_complete_octree():
     pos, mass = lattice(5)
     t, o = _check(pos, mass, 1)
