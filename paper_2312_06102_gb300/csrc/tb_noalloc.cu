@@ -45,7 +45,8 @@ constexpr size_t kOffKeys = align256(kOffLook + sizeof(uint64_t) * kLookWords);
 constexpr size_t kOffPerm = align256(kOffKeys + sizeof(uint64_t) * kNoAllocMaxN);
 constexpr size_t kOffXm = align256(kOffPerm + sizeof(int32_t) * kNoAllocMaxN);
 constexpr size_t kOffRuns = align256(kOffXm + 16 * size_t(kNoAllocMaxN));
-constexpr size_t kRunsCap = kNoAllocMaxN / 1024 + 2;   // long sort runs (> 1024 keys)
+// queue of long sort runs (over 128 keys) and one flag byte per 2048 keys
+constexpr size_t kRunsCap = kNoAllocMaxN / 128 + 2 + (kNoAllocMaxN / 2048 + 4) / 4 + 1;
 constexpr size_t kScratchBytes = align256(kOffRuns + sizeof(int32_t) * kRunsCap);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
