@@ -59,6 +59,140 @@ __global__ void __launch_bounds__(kLvThreads, 2)
     if (threadIdx.x < kLevelFields) tile_cnt[(int64_t)threadIdx.x * n_tiles + t] = tot[threadIdx.x];
 }
 
+// The same counts, four consecutive particles per thread, for n_crit in
+// [kLcMinN, kLcMaxN].  A block takes two count tiles.  c is kept one byte per
+// position; the window maxima of four neighbours share all but their ends:
+// L_{k0+j} = max(suffix max from byte j of c[k0-n .. k0-n+3],
+//                max of c[k0-n+4 .. k0-1],
+//                prefix max to byte j of c[k0 .. k0+3]),
+// taken four bytes at a time (byte-wise SIMD maxima).  The per-level counts
+// come from histograms of m and of L + 1 over the leaf starts:
+// #cells started at level d = #{m <= d} - #{L + 1 <= d}.
+constexpr int kLcThreads = 512;
+constexpr int kLcPer = 4;
+constexpr int kLcSub = 2;                               // count tiles per block
+constexpr int kLcTile = kLvTile * kLcSub;
+constexpr int kLcMinN = 3, kLcMaxN = 60;
+
+__host__ __device__ inline int lc_halo_words(int ncrit) { return (ncrit + 3) / 4 + 1; }
+__host__ __device__ inline size_t lc_smem_bytes(int ncrit) {
+    const size_t nk = (size_t)kLcTile + 4 * lc_halo_words(ncrit) + ncrit + 4;   // keys
+    const size_t nw = (size_t)kLcTile / 4 + lc_halo_words(ncrit) + 2;          // c words
+    return nk * 8 + nw * 4;
+}
+
+__global__ void __launch_bounds__(kLcThreads, 3)
+    level_count_fast_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
+                            uint32_t *__restrict__ tile_cnt, int64_t n_tiles,
+                            uint16_t *__restrict__ ml) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    __shared__ uint32_t hist_m[kLcSub][kLevels + 1];    // leaf starts by m
+    __shared__ uint32_t hist_l[kLcSub][kLevels + 1];    // leaf starts by L + 1
+    const int H = lc_halo_words(ncrit);
+    const int64_t s = (int64_t)blockIdx.x * kLcTile, e = min64(n, s + kLcTile);
+    const int64_t base = s - 4 * H;                     // position of key[0] and of c byte 0
+    const int nk = (int)(e + ncrit - base);
+    const int nw = (int)((e - base + 3) / 4);
+    uint64_t *key = reinterpret_cast<uint64_t *>(raw);
+    uint32_t *cw = reinterpret_cast<uint32_t *>(raw + ((size_t)kLcTile + 4 * H + ncrit + 4) * 8);
+    for (int x = threadIdx.x; x < nk; x += kLcThreads) {
+        const int64_t i = base + x;
+        key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
+    }
+    for (int x = threadIdx.x; x < kLcSub * (kLevels + 1); x += kLcThreads) {
+        (&hist_m[0][0])[x] = 0;
+        (&hist_l[0][0])[x] = 0;
+    }
+    __syncthreads();
+    // c of four positions per word: min(21, minDepth(i, i+n)) where the
+    // window exists, else 0
+    for (int w = threadIdx.x; w < nw; w += kLcThreads) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = 4 * w + j;
+            const int64_t i = base + x;
+            if (i >= 0 && i + ncrit < n && i < e)
+                v |= (uint32_t)min(kDepthMax, min_depth(key[x], key[x + ncrit])) << (8 * j);
+        }
+        cw[w] = v;
+    }
+    __syncthreads();
+    const int64_t k0 = s + kLcPer * threadIdx.x;
+    uint32_t Lw = 0, mw = 0xffffffffu;                  // bytes: L and m of k0 .. k0 + 3
+    if (k0 < e) {
+        const int x0 = (int)(k0 - base);                // multiple of 4
+        const uint32_t T = cw[x0 >> 2];
+        auto bytes4 = [&](int b) {                      // c bytes b .. b + 3 (b >= 0)
+            const int w = b >> 2, sh = (b & 3) * 8;
+            return sh ? __funnelshift_r(cw[w], cw[w + 1], sh) : cw[w];
+        };
+        const uint32_t Hw = bytes4(x0 - ncrit);
+        uint32_t I = 0;
+        const int mlen = ncrit - 4;                     // middle bytes x0 - n + 4 .. x0 - 1
+        if (mlen >= 4) {
+            for (int b = x0 - ncrit + 4; b + 4 <= x0; b += 4) I = __vmaxu4(I, bytes4(b));
+            I = __vmaxu4(I, bytes4(x0 - 4));
+        } else if (mlen > 0) {
+            I = bytes4(x0 - ncrit + 4) & ((1u << (8 * mlen)) - 1u);
+        }
+        I = __vmaxu4(I, I >> 16);
+        I = __vmaxu4(I, I >> 8);
+        I = (I & 0xffu) * 0x01010101u;
+        uint32_t S = __vmaxu4(Hw, Hw >> 8);
+        S = __vmaxu4(S, S >> 16);
+        uint32_t P = __vmaxu4(T, T << 8);
+        P = __vmaxu4(P, P << 16);
+        Lw = __vmaxu4(__vmaxu4(S, P), I);
+        mw = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t k = k0 + j;
+            uint32_t m = 255u;
+            if (k < e) m = (k == 0) ? 0u : (uint32_t)min_depth(key[x0 + j - 1], key[x0 + j]);
+            mw |= m << (8 * j);
+        }
+        // m and L of the four particles, for the emission
+        if (k0 + 4 <= e) {
+            uint2 v;
+            v.x = (mw & 0xffu) | ((Lw & 0xffu) << 8) | (((mw >> 8) & 0xffu) << 16) | (((Lw >> 8) & 0xffu) << 24);
+            v.y = ((mw >> 16) & 0xffu) | (((Lw >> 16) & 0xffu) << 8) | ((mw >> 24) << 16) | ((Lw >> 24) << 24);
+            *reinterpret_cast<uint2 *>(ml + k0) = v;
+        } else {
+            for (int j = 0; j < 4 && k0 + j < e; ++j)
+                ml[k0 + j] = (uint16_t)(((mw >> (8 * j)) & 0xffu) | (((Lw >> (8 * j)) & 0xffu) << 8));
+        }
+    }
+    // histograms of m and L + 1 over the leaf starts (m <= L), one atomic per
+    // distinct value and warp
+    const int sub = (int)(kLcPer * threadIdx.x / kLvTile);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int m = (mw >> (8 * j)) & 0xff, L = (Lw >> (8 * j)) & 0xff;
+        const bool start = m <= L;
+        const int km = start ? m : 31, kl = start ? L + 1 : 31;
+        const unsigned pm = __match_any_sync(0xffffffffu, km);
+        const unsigned pl = __match_any_sync(0xffffffffu, kl);
+        const int lane = threadIdx.x & 31;
+        if (start && lane == __ffs(pm) - 1) atomicAdd(&hist_m[sub][km], (uint32_t)__popc(pm));
+        if (start && lane == __ffs(pl) - 1) atomicAdd(&hist_l[sub][kl], (uint32_t)__popc(pl));
+    }
+    __syncthreads();
+    if (threadIdx.x < kLcSub * kLevelFields) {
+        const int sb = threadIdx.x / kLevelFields, f = threadIdx.x % kLevelFields;
+        const int64_t t = (int64_t)blockIdx.x * kLcSub + sb;
+        if (t < n_tiles) {
+            uint32_t v = 0;
+            if (f == kLevels) {
+                for (int d = 0; d < kLevels; ++d) v += hist_m[sb][d];
+            } else {
+                for (int d = 0; d <= f; ++d) v += hist_m[sb][d] - hist_l[sb][d];
+            }
+            tile_cnt[(int64_t)f * n_tiles + t] = v;
+        }
+    }
+}
+
 // One block per field: exclusive prefix over tiles (in place); the last block
 // to finish turns the field totals into level offsets.
 constexpr int kScanThreads = 1024;
@@ -181,8 +315,23 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int ncrit, Workspace
                              cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
-    level_count_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt,
-                                                                 tiles, ws.ml);
+    if (ncrit >= kLcMinN && ncrit <= kLcMaxN) {
+        static bool fast_attr = false;
+        if (!fast_attr) {
+            cudaFuncSetAttribute(level_count_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lc_smem_bytes(kLcMaxN));
+            cudaFuncSetAttribute(level_count_fast_kernel,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+            fast_attr = true;
+        }
+        const int64_t blocks = (n + kLcTile - 1) / kLcTile;
+        level_count_fast_kernel<<<(unsigned)blocks, kLcThreads, lc_smem_bytes(ncrit), s>>>(
+            skeys, n, ncrit, ws.level_cnt, tiles, ws.ml);
+    } else {
+        level_count_kernel<<<(unsigned)tiles, kLvThreads, smem, s>>>(skeys, n, ncrit, ws.level_cnt,
+                                                                     tiles, ws.ml);
+    }
     ++g_launches;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;

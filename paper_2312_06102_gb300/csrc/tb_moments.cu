@@ -81,15 +81,30 @@ __global__ void __launch_bounds__(kMomThreads, 3)
 }
 
 // The non-leaf cells of level d, from their children (finished by the
-// launch for level d + 1, or by the leaf launches).
+// launch for level d + 1, or by the leaf launches).  Each warp takes 64
+// consecutive cells and packs their non-leaf ones, in order, onto its lanes.
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads, 3)
     level_moments_kernel(TreeIn T, MomOut o, DevInfo *info, int d) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    __shared__ int32_t s_list[kMomThreads / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += stride)
-        if (T.child_first[c] >= 0) combine_children<MODE>(T, o, c);
+    const int64_t nwarps = (int64_t)gridDim.x * (kMomThreads / 32);
+    const unsigned lt = lanemask_lt();
+    for (int64_t base = lo + ((int64_t)blockIdx.x * (kMomThreads / 32) + warp) * 64; base < hi;
+         base += nwarps * 64) {
+        const int64_t c0 = base + lane, c1 = base + 32 + lane;
+        const bool p0 = c0 < hi && T.child_first[c0] >= 0;
+        const bool p1 = c1 < hi && T.child_first[c1] >= 0;
+        const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+        if (p0) s_list[warp][__popc(b0 & lt)] = (int32_t)c0;
+        if (p1) s_list[warp][__popc(b0) + __popc(b1 & lt)] = (int32_t)c1;
+        __syncwarp();
+        const int cnt = __popc(b0) + __popc(b1);
+        for (int k = lane; k < cnt; k += 32) combine_children<MODE>(T, o, s_list[warp][k]);
+        __syncwarp();
+    }
 }
 
 // Block-wide sums of the long depth-21 leaves queued by the leaf launch.

@@ -60,6 +60,31 @@ struct AccC {
                 Qc[j] += e + qe;
             }
     }
+    // a child cell of mass m, centre ref + (h + l), central second moment q:
+    // its mass, first moment and second moment about the reference point
+    __device__ void add_cell(float m, const float h[3], const float l[3], const float q[6]) {
+        float e;
+        two_sum(M, m, M, e);
+        Mc += e;
+        float p[3], pe[3];
+        for (int a = 0; a < 3; ++a) {
+            two_prod(m, h[a], p[a], pe[a]);
+            pe[a] = __fmaf_rn(m, l[a], pe[a]);
+            two_sum(S[a], p[a], S[a], e);
+            Sc[a] += e + pe[a];
+        }
+        int j = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b, ++j) {
+                float e1, t, te;
+                two_sum(Q[j], q[j], Q[j], e1);
+                two_prod(p[a], h[b], t, te);
+                te = __fmaf_rn(pe[a], h[b], te);
+                te = __fmaf_rn(p[a], l[b], te);
+                two_sum(Q[j], t, Q[j], e);
+                Qc[j] += (e1 + e) + te;
+            }
+    }
     // merge another accumulator of the same reference point
     __device__ void merge(const AccC &o) {
         float e;
@@ -131,7 +156,13 @@ __device__ void write_cell_f32(const MomOut &o, int64_t c, float M, const float 
                                const float cl[3], const float Q[6], const float bb[6]) {
     o.mass[c] = M;
     for (int a = 0; a < 3; ++a) { o.com[3 * c + a] = ch[a]; o.com_lo[3 * c + a] = cl[a]; }
-    for (int j = 0; j < 6; ++j) { o.quad[6 * c + j] = Q[j]; o.aabb[6 * c + j] = bb[j]; }
+    // quad and aabb rows are 24 bytes, 8-byte aligned
+    float2 *q2 = reinterpret_cast<float2 *>(o.quad + 6 * c);
+    float2 *b2 = reinterpret_cast<float2 *>(o.aabb + 6 * c);
+    for (int j = 0; j < 3; ++j) {
+        q2[j] = make_float2(Q[2 * j], Q[2 * j + 1]);
+        b2[j] = make_float2(bb[2 * j], bb[2 * j + 1]);
+    }
 }
 
 __device__ void write_cell_f64(const MomOut &o, int64_t c, double M, const double com[3],
@@ -211,6 +242,32 @@ __device__ void finish_d(const MomOut &o, int64_t c, const AccD &A, const float 
 
 // ------------------------------------------------------------- leaves
 
+// Compensated-mode leaves of at most this many members are summed with two
+// interleaved plain FP32 accumulators (even and odd members) instead.  With
+// u = 2^-24 and every member within one cell side s of the reference point on
+// each axis, each half-sum of at most 8 terms plus its products and the final
+// merge err by at most 9 u sum|terms|: 9 u M on the mass, 10 u s on the
+// centre of mass, 12 u M s^2 on the second moment (1e-6 s and 1e-6 M s^2 or
+// less), inside the tolerances the compensated parents carry upward.
+constexpr int kSplitLeaf = 16;
+
+__device__ void finish_split(const MomOut &o, int64_t c, const AccP &A, const AccP &B,
+                             const float ref[3], const float bb[6]) {
+    const float M = __fadd_rn(A.M, B.M);
+    float r[3], Q[6], ch[3], cl[3];
+    for (int a = 0; a < 3; ++a) r[a] = (M != 0.f) ? __fdiv_rn(__fadd_rn(A.S[a], B.S[a]), M) : 0.f;
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++j)
+            Q[j] = __fmaf_rn(-__fmul_rn(M, r[a]), r[b], __fadd_rn(A.Q[j], B.Q[j]));
+    for (int a = 0; a < 3; ++a) {
+        float h, l;
+        two_sum(ref[a], r[a], h, l);
+        fast_two_sum(h, l, ch[a], cl[a]);
+    }
+    write_cell_f32(o, c, M, ch, cl, Q, bb);
+}
+
 // Sum the members [pf, pe) of one leaf from the key-ordered records; loads
 // are issued four at a time before any is used.  Leaves reaching this path
 // hold at most 2048 particles (longer ones, only possible at depth 21, go to
@@ -222,6 +279,35 @@ __device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t
     const float4 r0 = xs[pf];
     const float ref[3] = {r0.x, r0.y, r0.z};
     float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+    if constexpr (MODE == TB_MOM_FP32_COMP) {
+        if (pe - pf <= kSplitLeaf) {
+            AccP A, B;
+            A.init();
+            B.init();
+            for (int64_t k0 = pf; k0 < pe; k0 += G) {
+                const int cnt = (int)min64(G, pe - k0);
+                float4 v[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    if (j < cnt) v[j] = xs[k0 + j];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if (j >= cnt) break;
+                    const float x[3] = {v[j].x, v[j].y, v[j].z};
+                    for (int a = 0; a < 3; ++a) {
+                        bb[a] = fminf(bb[a], x[a]);
+                        bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+                    }
+                    const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
+                                         __fsub_rn(x[2], ref[2])};
+                    if (j & 1) B.add(v[j].w, dx);
+                    else A.add(v[j].w, dx);
+                }
+            }
+            finish_split(o, c, A, B, ref, bb);
+            return;
+        }
+    }
     typename std::conditional<MODE == TB_MOM_FP64, AccD,
                               typename std::conditional<MODE == TB_MOM_FP32_COMP, AccC,
                                                         AccP>::type>::type A;
@@ -318,79 +404,51 @@ __device__ __noinline__ void combine_f64(const MomOut &o, int64_t p, int32_t c0,
 template <int MODE>
 __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
     const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
-    float bb[6];
-    for (int a = 0; a < 6; ++a) bb[a] = o.aabb[6 * (int64_t)c0 + a];
-    for (int32_t c = c0 + 1; c < c1; ++c)
+    // six floats of cell c (quad, aabb: rows of 24 bytes, 8-byte aligned)
+    auto row6 = [](const float *base, int64_t c, float v[6]) {
+        const float2 *r = reinterpret_cast<const float2 *>(base + 6 * c);
+        const float2 x = r[0], y = r[1], z = r[2];
+        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y; v[4] = z.x; v[5] = z.y;
+    };
+    auto grow = [](float bb[6], const float cb[6]) {
         for (int a = 0; a < 3; ++a) {
-            bb[a] = fminf(bb[a], o.aabb[6 * (int64_t)c + a]);
-            bb[3 + a] = fmaxf(bb[3 + a], o.aabb[6 * (int64_t)c + 3 + a]);
+            bb[a] = fminf(bb[a], cb[a]);
+            bb[3 + a] = fmaxf(bb[3 + a], cb[3 + a]);
         }
+    };
+    float bb[6];
+    row6(o.aabb, c0, bb);
     const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
+    if constexpr (MODE == TB_MOM_FP32_COMP) {
+        if (!big) {
+            // one pass: mass, first and second moments about the first
+            // child's centre, then the shift to the centre of mass (as for a
+            // leaf)
+            float ref[3];
+            for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
+            AccC A;
+            A.init();
+            for (int32_t c = c0; c < c1; ++c) {
+                float h[3], l[3], q[6], cb[6];
+                for (int a = 0; a < 3; ++a) child_offset(o, c, a, ref[a], h[a], l[a]);
+                row6(o.quad, c, q);
+                if (c > c0) {
+                    row6(o.aabb, c, cb);
+                    grow(bb, cb);
+                }
+                A.add_cell(o.mass[c], h, l, q);
+            }
+            finish_c(o, p, A, ref, bb);
+            return;
+        }
+    }
+    for (int32_t c = c0 + 1; c < c1; ++c) {
+        float cb[6];
+        row6(o.aabb, c, cb);
+        grow(bb, cb);
+    }
     if (MODE == TB_MOM_FP64 || big) {
         combine_f64<MODE>(o, p, c0, c1, bb);
-    } else if constexpr (MODE == TB_MOM_FP32_COMP) {
-        float ref[3];
-        for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
-        // pass 1: mass and first moment about ref
-        float Mh = 0.f, Mc = 0.f, Sh[3] = {0, 0, 0}, Sc[3] = {0, 0, 0};
-        for (int32_t c = c0; c < c1; ++c) {
-            float m = o.mass[c], e;
-            two_sum(Mh, m, Mh, e);
-            Mc += e;
-            for (int a = 0; a < 3; ++a) {
-                float h, l, pp, pe;
-                child_offset(o, c, a, ref[a], h, l);
-                two_prod(m, h, pp, pe);
-                pe = __fmaf_rn(m, l, pe);
-                two_sum(Sh[a], pp, Sh[a], e);
-                Sc[a] += e + pe;
-            }
-        }
-        float MH, ML;
-        fast_two_sum(Mh, Mc, MH, ML);
-        float rh[3], rl[3];
-        for (int a = 0; a < 3; ++a) {
-            float sh, sl;
-            fast_two_sum(Sh[a], Sc[a], sh, sl);
-            if (MH != 0.f) df_div(sh, sl, MH, ML, rh[a], rl[a]);
-            else rh[a] = rl[a] = 0.f;
-        }
-        // pass 2: second moment with the parallel-axis shift
-        float Q[6], Qc[6];
-        for (int q = 0; q < 6; ++q) Q[q] = Qc[q] = 0.f;
-        for (int32_t c = c0; c < c1; ++c) {
-            const float m = o.mass[c];
-            float e[3];
-            for (int a = 0; a < 3; ++a) {
-                float h, l;
-                child_offset(o, c, a, ref[a], h, l);
-                e[a] = __fadd_rn(__fsub_rn(h, rh[a]), __fsub_rn(l, rl[a]));
-            }
-            int q = 0;
-            for (int a = 0; a < 3; ++a)
-                for (int b = a; b < 3; ++b, ++q) {
-                    float sum, er;
-                    two_sum(Q[q], o.quad[6 * (int64_t)c + q], sum, er);
-                    Q[q] = sum;
-                    Qc[q] += er;
-                    float t, te, pp, pe;
-                    two_prod(m, e[a], t, te);
-                    two_prod(t, e[b], pp, pe);
-                    pe = __fmaf_rn(te, e[b], pe);
-                    two_sum(Q[q], pp, sum, er);
-                    Q[q] = sum;
-                    Qc[q] += er + pe;
-                }
-        }
-        float Qf[6], ch[3], cl[3];
-        for (int q = 0; q < 6; ++q) Qf[q] = __fadd_rn(Q[q], Qc[q]);
-        for (int a = 0; a < 3; ++a) {
-            float h, l;
-            two_sum(ref[a], rh[a], h, l);
-            l = __fadd_rn(l, rl[a]);
-            fast_two_sum(h, l, ch[a], cl[a]);
-        }
-        write_cell_f32(o, p, MH + ML, ch, cl, Qf, bb);
     } else {
         float ref[3];
         for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kRunThreads)
         const bool st = x >= nw || ((sk[x + 2] ^ sk[x + 1]) >= lim);
         const uint32_t m = __ballot_sync(0xffffffffu, st);
         if (lane == 0) smask[c] = m;
-        multi |= (m != 0xffffffffu) && c * 32 < te;
+        multi |= (m != 0xffffffffu) && c * 32 <= te;   // includes position te (a run from te - 1)
     }
     // a tile of single-key runs is done
     if (!__syncthreads_or(multi)) {

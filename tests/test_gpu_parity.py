@@ -108,6 +108,35 @@ def test_long_sort_runs(radix_bits):
     assert counts.max() > 4096
 
 
+def _runs_at_tile_ends():
+    """Lattice points (every one alone in its depth-13 cell) plus, for each of
+    several run-step tiles (2048 keys), two more points in the cell of the
+    key that sorts last in the tile: a run of three equal upper-bit keys that
+    starts at the tile's last position and whose order needs the low bits."""
+    g = np.arange(20)
+    pts = (np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + 0.5) / 20.0
+    pts = np.concatenate([pts, [[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]]])
+    for end in (2047, 4095, 6143):
+        k, _, _ = oracle.keys(pts.astype(np.float32))
+        i = np.argsort(k, kind="stable")[end]
+        pts = np.concatenate([pts, pts[i] + np.array([[2e-6, 1e-6, 3e-6], [1e-6, 3e-6, 1e-6]])])
+    pos = pts.astype(np.float32)
+    sk = np.sort(oracle.keys(pos)[0])
+    top = sk >> np.uint64(23)
+    starts = np.flatnonzero(np.concatenate([[True], top[1:] != top[:-1]]))
+    lens = np.diff(np.concatenate([starts, [len(sk)]]))
+    assert set(starts[lens > 1].tolist()) == {2047, 4095, 6143}
+    return pos
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_sort_runs_from_tile_end(order):
+    pos = _runs_at_tile_ends()
+    if order:
+        pos = pos[::-1].copy()
+    _check(pos, None, 4)
+
+
 def test_lattice_complete_octree():
     pos, mass = lattice(5)
     t, o = _check(pos, mass, 1)
