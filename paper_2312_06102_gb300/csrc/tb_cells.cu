@@ -194,40 +194,69 @@ __global__ void __launch_bounds__(kLcThreads, 3)
 }
 
 // One block per field: exclusive prefix over tiles (in place); the last block
-// to finish turns the field totals into level offsets.
+// to finish turns the field totals into level offsets.  The row is taken in
+// chunks staged in shared memory (coalesced loads and stores), each thread
+// scanning a contiguous stretch of a chunk.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+static_assert(kScanPer == 8, "the scan moves each thread's eight counts as two uint4");
 
 __global__ void __launch_bounds__(kScanThreads)
     level_scan_kernel(uint32_t *tile_cnt, int64_t n_tiles, DevInfo *info, int64_t cell_cap) {
     const int f = blockIdx.x;
     uint32_t *row = tile_cnt + (int64_t)f * n_tiles;
-    const int64_t per = (n_tiles + kScanThreads - 1) / kScanThreads;
-    const int64_t lo = threadIdx.x * per, hi = min64(n_tiles, lo + per);
-    uint64_t sum = 0;
-    for (int64_t i = lo; i < hi; ++i) sum += row[i];
-    // block exclusive scan of `sum`
-    __shared__ uint64_t s_w[kScanThreads / 32];
-    __shared__ uint64_t s_total;
+    __shared__ __align__(16) uint32_t s_v[kScanChunk];
+    __shared__ uint32_t s_w[kScanThreads / 32];
+    __shared__ uint64_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t x = sum;
-    for (int off = 1; off < 32; off <<= 1) {
-        uint64_t y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
+    if (threadIdx.x == 0) s_carry = 0;
+    for (int64_t c0 = 0; c0 < n_tiles; c0 += kScanChunk) {
+        const int len = (int)min64(kScanChunk, n_tiles - c0);
+        for (int i = threadIdx.x; i < kScanChunk; i += kScanThreads) s_v[i] = i < len ? row[c0 + i] : 0u;
+        __syncthreads();
+        uint32_t v[kScanPer], sum = 0;
+        {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(s_v) + 2 * threadIdx.x;
+            const uint4 a = s4[0], b = s4[1];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        }
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) sum += v[j];
+        uint32_t x = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_w[lane];
+            uint32_t z = w;
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, off);
+                if (lane >= off) z += y;
+            }
+            s_w[lane] = z - w;
+        }
+        __syncthreads();
+        // the per-field counts fit 32 bits (at most 2^31 particles)
+        uint32_t run = (uint32_t)s_carry + s_w[warp] + x - sum;
+        uint32_t o[kScanPer];
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) { o[j] = run; run += v[j]; }
+        {
+            uint4 *s4 = reinterpret_cast<uint4 *>(s_v) + 2 * threadIdx.x;
+            s4[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            s4[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += kScanThreads) row[c0 + i] = s_v[i];
+        if (threadIdx.x == kScanThreads - 1) s_carry = run;
+        __syncthreads();
     }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t r = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) { uint64_t v = s_w[w]; s_w[w] = r; r += v; }
-        s_total = r;
-    }
-    __syncthreads();
-    uint64_t run = s_w[warp] + x - sum;
-    for (int64_t i = lo; i < hi; ++i) {
-        uint32_t v = row[i];
-        row[i] = (uint32_t)run;
-        run += v;
-    }
+    const uint64_t s_total = s_carry;
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
         // totals land in a small array right after the per-tile rows
