@@ -42,7 +42,11 @@ from synth import WORKLOADS, batched_plummer, workload  # noqa: E402
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
 # the digest of the kernel source it was taken on; reported only while the
 # source is unchanged (see profiles/).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # onesweep pass <8, 512, 8>, N = 2^25 clustered, passes 2 and 3 of a timed
+    # build: dram__bytes_read.sum + dram__bytes_write.sum, mean of the two
+    "fb26802ac49effb8": {"bytes": 770.81e6, "n": 1 << 25, "variant": (8, 512, 8)},
+}
 
 METRIC = "tree-build Mparticles/s + HBM roofline %; batched vs plain on same GB300"
 
@@ -295,11 +299,15 @@ def run_ours(a):
     avg_launch_s = sort_ms / max(1, sort_launches) / 1e3
     achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     dig = kernel_digest()
-    traffic = NCU_TRAFFIC.get(dig)
+    rec = NCU_TRAFFIC.get(dig)
+    # scaled by the keys per launch (the capture's inputs are 3x L2 already)
+    traffic = None
+    if rec is not None and cfg is not None and tuple(cfg) == rec["variant"]:
+        traffic = rec["bytes"] * n / rec["n"]
     roofline = {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_kind": peak_kind,
-                "traffic": None if traffic is None else round(traffic * n / traffic_n(dig)),
+                "traffic": None if traffic is None else round(traffic),
                 "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "mean_launch_ms": round(avg_launch_s * 1e3, 4)}
     # whole-build bytes: positions read twice (root cell, keys), positions and
@@ -374,10 +382,6 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
-
-
-def traffic_n(dig):
-    return 1
 
 
 _MASK64 = (1 << 64) - 1
