@@ -72,6 +72,7 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-reorder", action="store_true", help="skip the key-ordered-input build")
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--precision", action="store_true",
                     help="print the per-level moment error of the three modes against the oracle")
@@ -364,6 +365,44 @@ def run_ours(a):
         out["e2e"] = {"value": round(n * a.steps * world / (ems / 1e3) / 1e6, 2),
                       "unit": "Mparticles/s", "h2d_bytes_per_step": int(16 * n),
                       "d2h_bytes_per_step": 40}
+
+    # key-ordered input: what a simulation sees when it reorders its particle
+    # arrays every few steps (tb_reorder), so the build's gather is local
+    if not a.no_reorder:
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        pr = tb.reorder(tree, p)
+        wr = tb.reorder(tree, w)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        reorder_ms = r0.elapsed_time(r1)
+        tree2 = tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg)
+        tb.moments(tree2, pr, wr)
+        torch.cuda.synchronize()
+        for _ in range(a.warmup):
+            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2)
+            tb.moments(tree2, pr, wr)
+        torch.cuda.synchronize()
+        r0.record(stream)
+        for _ in range(a.steps):
+            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2)
+            tb.moments(tree2, pr, wr)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        kms = r0.elapsed_time(r1) / a.steps
+        ok = tree2.sync() == 0 and tree2.n_cells == C
+        out["key_ordered_input"] = {
+            "reorder_ms_pos_and_mass": round(reorder_ms, 4),
+            "build_ms": round(kms, 4),
+            "mparticles_s": round(n / (kms / 1e3) / 1e6, 2),
+            "same_cell_count": bool(ok),
+            "note": "positions and masses reordered into key order by tb_reorder, then "
+                    "built again (the same tree, identity permutation)"}
+        tree2.free()
+        del pr, wr
 
     if not a.no_batched and world == 1:
         try:

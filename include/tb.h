@@ -168,6 +168,21 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
                            int32_t n_sets, int64_t n_total, const tb_params *params,
                            tb_stream stream, tb_tree **tree);
 
+/* Reorder a per-particle array into the key order of a built single tree
+ * (Sec. 2.3 step 3; done "every few steps" in a simulation so that later
+ * builds start from nearly sorted particles):
+ *   d_dst[k] = d_src[perm[k]] for k < n_particles, row by row.
+ *   d_src, d_dst  [n_particles][row_bytes] device arrays, caller-owned; they
+ *                 must not overlap; 4-byte aligned (16-byte rows on 16-byte
+ *                 aligned arrays take the vector path)
+ *   row_bytes     bytes per particle, a positive multiple of 4 (e.g. 12 for
+ *                 [n][3] FP32 positions, 4 for masses)
+ * The tree must come from tb_build (not tb_build_batched); its perm is read
+ * on `stream`, so the build must be ordered before this call.  Returns TB_OK
+ * or TB_EINVAL (bad pointer, size or alignment) / TB_ECUDA. */
+tb_status tb_reorder(const tb_tree *tree, const void *d_src, void *d_dst, int64_t row_bytes,
+                     tb_stream stream);
+
 /* Release a tree (NULL-safe).  Synchronises with the device before freeing. */
 void tb_free(tb_tree *tree);
 

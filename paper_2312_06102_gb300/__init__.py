@@ -25,6 +25,7 @@ from ._lib import (  # noqa: F401
     NOALLOC_MAX_N,
     kernel_launches,
     keys_sorted_noalloc,
+    reorder,
     lib,
     library_path,
     moments,

@@ -88,6 +88,8 @@ def lib():
         L.tb_sort_variant.restype = C.c_int32
         L.tb_keys_sorted_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, P(C.c_double), _vp]
         L.tb_keys_sorted_noalloc.restype = C.c_int
+        L.tb_reorder.argtypes = [P(TreeC), _vp, _vp, C.c_int64, _vp]
+        L.tb_reorder.restype = C.c_int
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
         L.tb_selftest_wait.restype = C.c_int
         _lib = L
@@ -277,6 +279,20 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
                                   _stream(stream), C.byref(t._p))
     _check(code, "tb_build_batched")
     return t
+
+
+def reorder(tree: Tree, src: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """tb_reorder: out[k] = src[perm[k]] for a per-particle CUDA tensor
+    (first dimension n_particles, contiguous, rows a multiple of 4 bytes)."""
+    if not src.is_cuda or not src.is_contiguous():
+        raise ValueError("src must be a contiguous CUDA tensor")
+    if out is None:
+        out = torch.empty_like(src)
+    n = src.shape[0]
+    row_bytes = src.numel() * src.element_size() // max(1, n)
+    code = lib().tb_reorder(tree._p, _ptr(src), _ptr(out), int(row_bytes), _stream(stream))
+    _check(code, "tb_reorder")
+    return out
 
 
 NOALLOC_MAX_N = 524288
