@@ -16,6 +16,7 @@ from .generators import (  # noqa: F401
     plummer,
     clustered_halos,
     precision_stress,
+    exponential_disk,
     batched_plummer,
     jitter_offsets,
     splitmix64,

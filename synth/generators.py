@@ -199,6 +199,33 @@ def batched_plummer(n_sets: int = 4096, seed: int = 4, nmin: int = 256, nmax: in
     return BatchedSets(pos=pos, mass=mass, offsets=offsets, scale=a, seed=seed)
 
 
+def exponential_disk(n: int, seed: int, rd: float = 0.05, z0: float = 0.005,
+                     rmax_over_rd: float = 10.0, zmax_over_z0: float = 10.0,
+                     centre: float = 0.5):
+    """Thin exponential disc in the x-y plane centred at (centre,)*3, equal
+    masses 1/n.  Surface density ~ exp(-R / rd): R / rd follows a Gamma(2, 1)
+    law (enclosed mass 1 - (1 + x) e^-x), redrawn beyond rmax_over_rd; azimuth
+    uniform; height z with density ~ sech^2(z / z0), z = z0 atanh(2u - 1),
+    redrawn beyond zmax_over_z0."""
+    rng = _rng(seed)
+    R = rd * rng.gamma(2.0, 1.0, n)
+    bad = R > rmax_over_rd * rd
+    while bad.any():
+        R[bad] = rd * rng.gamma(2.0, 1.0, int(bad.sum()))
+        bad = R > rmax_over_rd * rd
+    phi = rng.random(n) * (2.0 * math.pi)
+    z = z0 * np.arctanh(2.0 * rng.random(n) - 1.0)
+    bad = np.abs(z) > zmax_over_z0 * z0
+    while bad.any():
+        z[bad] = z0 * np.arctanh(2.0 * rng.random(int(bad.sum())) - 1.0)
+        bad = np.abs(z) > zmax_over_z0 * z0
+    pos = np.empty((n, 3))
+    pos[:, 0] = centre + R * np.cos(phi)
+    pos[:, 1] = centre + R * np.sin(phi)
+    pos[:, 2] = centre + z
+    return pos.astype(np.float32), _equal_masses(n)
+
+
 def splitmix64(x):
     """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays."""
     z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _MASK64
@@ -250,6 +277,7 @@ WORKLOADS = {
     "clustered_2p27": dict(kind="clustered", n=1 << 27, seed=3, n_crit=16),
     "batched_4096": dict(kind="batched", n_sets=4096, seed=4, n_crit=16),
     "stress_2p26": dict(kind="stress", n=1 << 26, seed=5, n_crit=16),
+    "disk_2p24": dict(kind="disk", n=1 << 24, seed=6, n_crit=16),
 }
 
 
@@ -263,4 +291,6 @@ def workload(kind: str, n: int | None = None, seed: int = 0, **kw):
         return clustered_halos(n, seed, **kw)
     if kind == "stress":
         return precision_stress(n, seed, **kw)
+    if kind == "disk":
+        return exponential_disk(n, seed, **kw)
     raise ValueError(f"unknown workload kind {kind!r}")

@@ -151,6 +151,18 @@ def test_plummer_2p24_full_oracle():
     assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
 
 
+def test_disk_2p24_full_oracle():
+    spec = WORKLOADS["disk_2p24"]
+    pos, mass = workload(spec["kind"], spec["n"], spec["seed"])
+    t = _build(pos, mass, 16, cfg=_bench_cfg(spec["n"]))
+    o = oracle.build_tree(pos, 16)
+    assert_structure_equal(t, o)
+    M, com, quad, aabb = oracle.moments(o, pos, mass)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+    assert bb_ok
+    assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
+
+
 @pytest.mark.parametrize("n_crit", [16, 8, 32])
 def test_clustered_2p27(n_crit):
     pos, mass, idx = _data("clustered_2p27")

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import clustered_halos, lattice, plummer, precision_stress, uniform_cube
+from synth import clustered_halos, exponential_disk, lattice, plummer, precision_stress, uniform_cube
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,14 @@ def test_radix_widths(radix_bits):
 def test_n_crit_values(n_crit):
     pos, mass = clustered_halos(60_000, 8, n_halo=200)
     _check(pos, mass, n_crit)
+
+
+@pytest.mark.parametrize("n_crit", [8, 16])
+def test_exponential_disc(n_crit):
+    """Thin disc (height 0.1 of the scale length): flat, anisotropic cells."""
+    pos, mass = exponential_disk(1 << 18, 16)
+    t, o = _check(pos, mass, n_crit)
+    assert t.max_depth >= 8
 
 
 def test_plummer_deep():
