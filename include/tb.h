@@ -168,6 +168,33 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
                            int32_t n_sets, int64_t n_total, const tb_params *params,
                            tb_stream stream, tb_tree **tree);
 
+/* Gravitational accelerations (G = 1) of every particle from the tree
+ * (Sec. 2.1): the Barnes-Hut walk with the opening test l / d < theta of Eq.
+ * 1, cells taken as monopole + quadrupole (use_quad != 0) or monopole only,
+ * and Barnes' modified algorithm -- the particles of a group share one
+ * interaction list.  Groups are the cells holding at most n_group particles
+ * whose parent holds more; a group is walked 32 particles at a time, and for
+ * each such chunk a cell is accepted when l < theta * d_min, with d_min the
+ * distance from the cell's centre of mass to the chunk's bounding box (so the
+ * test of Eq. 1 holds for every particle of the chunk), and never when its
+ * particles meet the chunk's.  Opened leaves contribute particle by particle.
+ * Point masses are Plummer-softened with length eps; the quadrupole term,
+ * T r / |r|^5 - (5/2) (r.T r) r / |r|^7 with T = 3 Q - tr(Q) I and r = x -
+ * COM, is not.  Arithmetic is FP32.
+ *   tree     a single tree (tb_build) whose moments are current (tb_moments
+ *            called after the last build), else TB_EINVAL
+ *   theta    opening parameter >= 0 (0 opens every cell: direct summation)
+ *   eps      softening length >= 0
+ *   n_group  group size bound, 1 <= n_group <= 2^20
+ *   d_acc    [n_particles][3] FP32 out, device, caller-owned, in the
+ *            caller's original particle order
+ * Scratch (groups and per-warp traversal stacks, about 30 MB plus 4 B per
+ * cell) is allocated on first use and kept with the tree.  A traversal stack
+ * that fills (not expected for trees of depth <= 21) sets a device status that
+ * tb_tree_status reports as TB_EOVERFLOW. */
+tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_t use_quad,
+                  float *d_acc, tb_stream stream);
+
 /* Reorder a per-particle array into the key order of a built single tree
  * (Sec. 2.3 step 3; done "every few steps" in a simulation so that later
  * builds start from nearly sorted particles):

@@ -26,6 +26,7 @@ from ._lib import (  # noqa: F401
     kernel_launches,
     keys_sorted_noalloc,
     reorder,
+    walk,
     lib,
     library_path,
     moments,

@@ -88,6 +88,8 @@ def lib():
         L.tb_sort_variant.restype = C.c_int32
         L.tb_keys_sorted_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, P(C.c_double), _vp]
         L.tb_keys_sorted_noalloc.restype = C.c_int
+        L.tb_walk.argtypes = [P(TreeC), C.c_float, C.c_float, C.c_int32, C.c_int32, _vp, _vp]
+        L.tb_walk.restype = C.c_int
         L.tb_reorder.argtypes = [P(TreeC), _vp, _vp, C.c_int64, _vp]
         L.tb_reorder.restype = C.c_int
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
@@ -279,6 +281,19 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
                                   _stream(stream), C.byref(t._p))
     _check(code, "tb_build_batched")
     return t
+
+
+def walk(tree: Tree, theta: float, eps: float, n_group: int = 32, use_quad: bool = True,
+         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """tb_walk: accelerations [n, 3] FP32 (original particle order) from the
+    tree; its moments must be current."""
+    n = tree.n
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    code = lib().tb_walk(tree._p, float(theta), float(eps), int(n_group), int(bool(use_quad)),
+                         _ptr(out), _stream(stream))
+    _check(code, "tb_walk")
+    return out
 
 
 def reorder(tree: Tree, src: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -65,7 +65,7 @@ tb_status from_dev(uint32_t st) {
     if (st & kErrInvalid) return TB_EINVAL;
     if (st & kErrNonFinite) return TB_ENONFINITE;
     if (st & kErrTimeout) return TB_ETIMEOUT;
-    if (st & kErrOverflow) return TB_EOVERFLOW;
+    if (st & (kErrOverflow | kErrWalk)) return TB_EOVERFLOW;
     return TB_OK;
 }
 
@@ -270,6 +270,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     const SortCfg cfg = pick_cfg(params);
     S->radix_bits = cfg.radix_bits;
     ws.last_stream = s;
+    ws.moments_ready = false;
     t.n_particles = n;
     t.n_crit = params->n_crit;
     ws.cell_cap_request = params->cell_capacity;
@@ -323,6 +324,26 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     return TB_OK;
 }
 
+tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_t use_quad,
+                  float *d_acc, tb_stream stream) {
+    if (!tree || tree->n_sets != 0 || !(theta >= 0.f) || !(theta < 1e30f) || !(eps >= 0.f) ||
+        !(eps < 1e30f) || n_group < 1 || n_group > (1 << 20))
+        return TB_EINVAL;
+    TreeState *S = state_of(tree);
+    if (tree->n_particles == 0) return TB_OK;
+    if (!d_acc || (reinterpret_cast<uintptr_t>(d_acc) & 3u)) return TB_EINVAL;
+    if (!S->ws.moments_ready) return TB_EINVAL;
+    const int64_t need = walk_buffer_words(tree->n_cells);
+    if (S->ws.walk_cap < need) {
+        dev_free(S->ws.walk);
+        S->ws.walk_cap = 0;
+        if (!dev_alloc(S->ws.walk, need)) return TB_ENOMEM;
+        S->ws.walk_cap = need;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return from_cuda(launch_walk(*tree, S->ws, theta, eps, n_group, use_quad, d_acc, S->ws.walk, s));
+}
+
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream) {
     if (!tree || (tree->n_particles > 0 && !d_pos)) return TB_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_pos) & 3u) return TB_EINVAL;
@@ -347,6 +368,7 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
     }
     e = launch_moments(*tree, S->ws, S->params.mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
+    S->ws.moments_ready = true;
     return TB_OK;
 }
 
@@ -446,6 +468,7 @@ void tb_free(tb_tree *tree) {
     dev_free(ws.info); dev_free(ws.hist); dev_free(ws.bbox_part);
     if (ws.h_info) cudaFreeHost(ws.h_info);
     for (cudaEvent_t e : ws.ev) cudaEventDestroy(e);
+    dev_free(ws.walk);
     dev_free(ws.set_order); dev_free(ws.set_cnt); dev_free(ws.set_leaf_off); dev_free(ws.set_ctr);
     dev_free(tree->set_particle_offset); dev_free(tree->set_cell_offset); dev_free(tree->set_root);
     delete S;

@@ -22,6 +22,7 @@ constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrOverflow = 2u;
 constexpr uint32_t kErrTimeout = 4u;
 constexpr uint32_t kErrInvalid = 8u;    // batched: set offsets not a partition of [0, n)
+constexpr uint32_t kErrWalk = 16u;      // tree walk: traversal stack full
 
 // Record of one build, in device memory; written by the kernels, read back
 // by the host after a synchronisation.
@@ -105,6 +106,10 @@ struct Workspace {
     uint32_t *set_ctr = nullptr;     // [4] work-queue tickets
 
     cudaStream_t last_stream = nullptr;
+    // tree walk scratch and whether the moments match the current structure
+    int32_t *walk = nullptr;
+    int64_t walk_cap = 0;
+    bool moments_ready = false;
 };
 
 // ------------------------------------------------------------ launchers
@@ -142,6 +147,11 @@ cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Wor
 cudaError_t launch_runs(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v, int64_t n,
                         int shift0, int32_t *long_runs, Workspace &ws, cudaStream_t s);
 int64_t long_run_capacity(int64_t n);
+
+// tree walk: int32 words of its scratch (counters, groups, per-warp stacks)
+int64_t walk_buffer_words(int64_t n_cells);
+cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps, int n_group,
+                        int use_quad, float *acc, int32_t *buf, cudaStream_t s);
 
 void mark(Workspace &ws, const char *name, cudaStream_t s);
 

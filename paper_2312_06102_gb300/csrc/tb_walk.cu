@@ -1,0 +1,261 @@
+// tb_walk.cu -- gravity from the built tree (Sec. 2.1): the Barnes-Hut walk
+// with the opening test l / d < theta of Eq. 1, monopole plus quadrupole, and
+// Barnes' modified algorithm, in which the particles of one small cell share
+// one interaction list.
+//
+//   walk_groups_kernel : the groups -- every cell holding at most n_group
+//                        particles whose parent holds more (the root if it
+//                        holds at most n_group), and every leaf holding more
+//                        (only depth-21 leaves of one key can);
+//   walk_kernel        : one warp per group (taken from an atomic ticket),
+//                        32 particles at a time (one per lane; a larger group
+//                        is walked in chunks of 32, each with its own box).
+//                        The warp walks the tree from the root, up to 32 cells
+//                        at a time: a cell whose particle range meets the chunk's is
+//                        always opened; any other cell is accepted when
+//                        l < theta * d_min, d_min the distance from its centre
+//                        of mass to the group's bounding box (so l / d < theta
+//                        holds for every particle of the group); an opened leaf
+//                        contributes its particles one by one.  Accepted cells
+//                        and opened leaves go to lists in shared memory; when a
+//                        list is full, and at the end, every lane evaluates the
+//                        lists for its particles of the group.
+// Forces (G = 1): a softened point mass m (r^2 + eps^2)^(-3/2) r for every
+// particle and cell; for a cell also the quadrupole term
+//   T r / |r|^5 - (5/2) (r.T r) r / |r|^7,  T = 3 Q - tr(Q) I,
+// with Q the cell's central second moment and r = x - COM (unsoftened).
+// Offsets are taken as (x - com) - com_lo, exact to one rounding when the
+// target and the centre are close.  The result is written in the caller's
+// particle order.
+#include "tb_device.cuh"
+
+namespace tb {
+
+namespace {
+
+constexpr int kWalkWarps = 4;
+constexpr int kWalkBlocks = 152 * 8;
+constexpr int kWalkThreads = 32 * kWalkWarps;
+// cells waiting to be tested, per warp in global memory: a round takes at most
+// 32 cells and adds at most 7 per cell, and only cells above depth 21 have
+// children, so the stack stays below 21 * 256 + 1 entries
+constexpr int kStackCap = 6144;
+constexpr int kCellCap = 256;       // accepted cells
+constexpr int kRangeCap = 128;      // particle ranges of opened leaves
+
+struct WalkTree {
+    const int32_t *child_first, *child_end, *pfirst, *pend;
+    const uint8_t *level;
+    const float *mass, *com, *com_lo, *quad, *aabb;
+    const float4 *xs;               // particles in key order: x, y, z, m
+    const int32_t *perm;
+    double side;
+};
+
+struct WarpLists {
+    int32_t cell[kCellCap];
+    int2 range[kRangeCap];
+};
+
+__device__ __forceinline__ float3 point_acc(float3 a, float rx, float ry, float rz, float m, float eps2) {
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
+    const float inv = rsqrtf(r2);
+    const float f = m * inv * inv * inv;
+    a.x = fmaf(-f, rx, a.x);
+    a.y = fmaf(-f, ry, a.y);
+    a.z = fmaf(-f, rz, a.z);
+    return a;
+}
+
+// the lists of one warp against its lane's particle k (when k < ke)
+__device__ float3 evaluate(const WalkTree &T, const WarpLists &W, int ncell, int nrange, int64_t k,
+                           int64_t ke, float eps2, bool use_quad, float3 a) {
+    const float4 x = k < ke ? T.xs[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < ncell; ++j) {
+        const int c = W.cell[j];
+        const float m = T.mass[c];
+        const float rx = (x.x - T.com[3 * c]) - T.com_lo[3 * c];
+        const float ry = (x.y - T.com[3 * c + 1]) - T.com_lo[3 * c + 1];
+        const float rz = (x.z - T.com[3 * c + 2]) - T.com_lo[3 * c + 2];
+        a = point_acc(a, rx, ry, rz, m, eps2);
+        if (use_quad) {
+            const float *q = T.quad + 6 * c;
+            const float tr = q[0] + q[3] + q[5];
+            const float txx = 3.f * q[0] - tr, tyy = 3.f * q[3] - tr, tzz = 3.f * q[5] - tr;
+            const float txy = 3.f * q[1], txz = 3.f * q[2], tyz = 3.f * q[4];
+            const float trx = txx * rx + txy * ry + txz * rz;
+            const float try_ = txy * rx + tyy * ry + tyz * rz;
+            const float trz = txz * rx + tyz * ry + tzz * rz;
+            const float rtr = rx * trx + ry * try_ + rz * trz;
+            const float ir2 = 1.f / (rx * rx + ry * ry + rz * rz);
+            const float ir5 = ir2 * ir2 * sqrtf(ir2);
+            const float s = 2.5f * rtr * ir5 * ir2;
+            a.x += trx * ir5 - s * rx;
+            a.y += try_ * ir5 - s * ry;
+            a.z += trz * ir5 - s * rz;
+        }
+    }
+    for (int j = 0; j < nrange; ++j) {
+        const int2 r = W.range[j];
+        for (int q = r.x; q < r.y; ++q) {
+            if (q == k) continue;                       // no self-force
+            const float4 y = T.xs[q];
+            a = point_acc(a, x.x - y.x, x.y - y.y, x.z - y.z, y.w, eps2);
+        }
+    }
+    return a;
+}
+
+__global__ void walk_groups_kernel(const int32_t *__restrict__ parent, const int32_t *__restrict__ child_first,
+                                   const int32_t *__restrict__ pfirst, const int32_t *__restrict__ pend,
+                                   int64_t n_cells, int n_group, int32_t *groups, uint32_t *ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        const int64_t cnt = (int64_t)pend[c] - pfirst[c];
+        const int32_t p = parent[c];
+        const bool small = cnt <= n_group && (p < 0 || (int64_t)pend[p] - pfirst[p] > n_group);
+        const bool big_leaf = child_first[c] < 0 && cnt > n_group;
+        if (small || big_leaf) groups[atomicAdd(&ctr[0], 1u)] = (int32_t)c;
+    }
+}
+
+__global__ void __launch_bounds__(kWalkThreads)
+    walk_kernel(WalkTree T, const int32_t *__restrict__ groups, uint32_t *ctr, int32_t *stacks,
+                float theta, float eps2, int use_quad, float *__restrict__ acc_out, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    __shared__ WarpLists lists[kWalkWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpLists &W = lists[warp];
+    int32_t *stack = stacks + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
+    const uint32_t ngroups = *(volatile const uint32_t *)&ctr[0];
+    const unsigned lt = lanemask_lt();
+    const float side = (float)T.side;
+    for (;;) {
+        uint32_t gi = 0;
+        if (lane == 0) gi = atomicAdd(&ctr[1], 1u);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= ngroups) return;
+        const int32_t g = groups[gi];
+        const int64_t gpf = T.pfirst[g], gpe = T.pend[g];
+        for (int64_t kb = gpf; kb < gpe; kb += 32) {
+            const int64_t ke = min64(gpe, kb + 32);
+            const int64_t k = kb + lane;
+            // bounding box of the chunk
+            float bmin[3], bmax[3];
+            {
+                const float4 x = T.xs[k < ke ? k : kb];
+                bmin[0] = bmax[0] = x.x;
+                bmin[1] = bmax[1] = x.y;
+                bmin[2] = bmax[2] = x.z;
+                for (int off = 16; off > 0; off >>= 1)
+                    for (int a = 0; a < 3; ++a) {
+                        bmin[a] = fminf(bmin[a], __shfl_xor_sync(0xffffffffu, bmin[a], off));
+                        bmax[a] = fmaxf(bmax[a], __shfl_xor_sync(0xffffffffu, bmax[a], off));
+                    }
+            }
+            float3 acc = make_float3(0.f, 0.f, 0.f);
+            int sp = 1, ncell = 0, nrange = 0;
+            if (lane == 0) stack[0] = 0;
+            __syncwarp();
+            bool overflow = false;
+            while (sp > 0) {
+                // room for this round: 32 accepted cells or leaf ranges, and
+                // 7 more stack entries per cell taken
+                if (ncell + 32 > kCellCap || nrange + 32 > kRangeCap) {
+                    acc = evaluate(T, W, ncell, nrange, k, ke, eps2, use_quad != 0, acc);
+                    ncell = nrange = 0;
+                    __syncwarp();
+                }
+                const int take = min(min(sp, 32), (kStackCap - sp) / 7);
+                if (take == 0) {
+                    overflow = true;
+                    break;
+                }
+                int c = -1;
+                if (lane < take) c = stack[sp - 1 - lane];
+                sp -= take;
+                __syncwarp();
+                int kind = 0;                           // 1 accept, 2 leaf, 3 open
+                int nch = 0, c0 = 0;
+                if (c >= 0) {
+                    const int32_t pf = T.pfirst[c], pe = T.pend[c];
+                    const bool meets = pf < ke && kb < pe;
+                    c0 = T.child_first[c];
+                    bool accept = false;
+                    if (!meets) {
+                        const float l = scalbnf(side, -(int)T.level[c]);
+                        float d2 = 0.f;
+                        for (int a = 0; a < 3; ++a) {
+                            const float x = T.com[3 * c + a] + T.com_lo[3 * c + a];
+                            const float u = fmaxf(fmaxf(bmin[a] - x, x - bmax[a]), 0.f);
+                            d2 = fmaf(u, u, d2);
+                        }
+                        accept = l * l < theta * theta * d2;
+                    }
+                    if (accept) kind = 1;
+                    else if (c0 < 0) kind = 2;
+                    else { kind = 3; nch = T.child_end[c] - c0; }
+                }
+                const unsigned ba = __ballot_sync(0xffffffffu, kind == 1);
+                const unsigned bl = __ballot_sync(0xffffffffu, kind == 2);
+                if (kind == 1) W.cell[ncell + __popc(ba & lt)] = c;
+                if (kind == 2) W.range[nrange + __popc(bl & lt)] = make_int2(T.pfirst[c], T.pend[c]);
+                ncell += __popc(ba);
+                nrange += __popc(bl);
+                // children onto the stack (exclusive scan of the counts)
+                int pos = nch;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, pos, off);
+                    if (lane >= off) pos += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, pos, 31);
+                pos -= nch;
+                for (int j = 0; j < nch; ++j) stack[sp + pos + j] = c0 + nch - 1 - j;
+                sp += total;
+                __syncwarp();
+            }
+            if (overflow) {
+                if (lane == 0) atomicOr(&info->status, kErrWalk);
+                return;
+            }
+            acc = evaluate(T, W, ncell, nrange, k, ke, eps2, use_quad != 0, acc);
+            __syncwarp();
+            if (k < ke) {
+                const int64_t i = T.perm[k];
+                acc_out[3 * i] = acc.x;
+                acc_out[3 * i + 1] = acc.y;
+                acc_out[3 * i + 2] = acc.z;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int64_t walk_buffer_words(int64_t n_cells) {
+    return 8 + n_cells + (int64_t)kWalkBlocks * kWalkWarps * kStackCap;
+}
+
+cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps, int n_group,
+                        int use_quad, float *acc, int32_t *buf, cudaStream_t s) {
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(buf);
+    int32_t *groups = buf + 8;
+    int32_t *stacks = groups + t.n_cells;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (t.n_cells + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    walk_groups_kernel<<<(unsigned)grid, 256, 0, s>>>(t.parent, t.child_first, t.pfirst, t.pend,
+                                                      t.n_cells, n_group, groups, ctr);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    WalkTree T{t.child_first, t.child_end, t.pfirst, t.pend, t.level, t.mass, t.com, t.com_lo,
+               t.quad, t.aabb, ws.xs, t.perm, t.side};
+    walk_kernel<<<kWalkBlocks, kWalkThreads, 0, s>>>(T, groups, ctr, stacks, theta, eps * eps,
+                                                     use_quad, acc, ws.info);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace tb

@@ -1,0 +1,104 @@
+"""tb_walk: the Barnes-Hut walk (Sec. 2.1, Eq. 1) with Barnes' modified
+groups, on the GPU.  It is checked against the oracle's FP64 direct sum
+(softening 1e-3 L, self-force excluded):
+  * theta = 0 opens every cell, so the walk is the direct sum itself, up to
+    FP32 rounding of N-term sums;
+  * theta = 0.5 with quadrupoles meets the bars of the oracle's own walk
+    (median relative error <= 1e-3, 99th percentile <= 1e-2);
+  * the GPU walk is no less accurate than the oracle's per-particle walk on
+    the same tree (its group test l < theta d_min is the stricter one), and
+    the quadrupole term lowers the error."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import clustered_halos, exponential_disk, plummer
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import tb, to_np, torch  # noqa: E402
+
+
+def _setup(pos, mass, n_crit=16):
+    m = tb()
+    p = torch.from_numpy(pos).cuda()
+    w = None if mass is None else torch.from_numpy(mass).cuda()
+    t = m.build(p, w, n_crit=n_crit)
+    m.moments(t, p, w)
+    torch.cuda.synchronize()
+    assert t.sync() == 0
+    return m, t
+
+
+def _rel(a, ref):
+    return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def _targets(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, min(n, k), replace=False)).astype(np.int64)
+
+
+@pytest.mark.parametrize("gen", ["plummer", "disc"])
+def test_theta_zero_is_the_direct_sum(gen):
+    n = 12_000
+    pos, mass = plummer(n, 41) if gen == "plummer" else exponential_disk(n, 41)
+    m, t = _setup(pos, mass)
+    eps = 1e-3 * t.side
+    acc = to_np(m.walk(t, 0.0, eps, n_group=32)).astype(np.float64)
+    tg = _targets(n, 300, 1)
+    ref = oracle.direct_acc(pos, mass, tg, eps)
+    e = _rel(acc[tg], ref)
+    # FP32 sums of 12,000 terms: a few sqrt(N) u in the median
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-3, (np.median(e), e.max())
+
+
+@pytest.mark.parametrize("n_group", [1, 32, 64, 200])
+def test_theta_half_meets_the_walk_bars(n_group):
+    n = 30_000
+    pos, mass = clustered_halos(n, 42, n_halo=40)
+    mass = (np.random.default_rng(3).random(n) + 0.5).astype(np.float32)
+    m, t = _setup(pos, mass)
+    eps = 1e-3 * t.side
+    acc = to_np(m.walk(t, 0.5, eps, n_group=n_group)).astype(np.float64)
+    tg = _targets(n, 400, 2)
+    e = _rel(acc[tg], oracle.direct_acc(pos, mass, tg, eps))
+    assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2, (np.median(e), np.percentile(e, 99))
+
+
+def test_no_worse_than_the_per_particle_walk_and_quadrupole_helps():
+    n = 20_000
+    pos, mass = plummer(n, 43)
+    m, t = _setup(pos, mass)
+    eps = 1e-3 * t.side
+    tg = _targets(n, 300, 3)
+    ref = oracle.direct_acc(pos, mass, tg, eps)
+    o = oracle.build_tree(pos, 16)
+    M, com, quad, _ = oracle.moments(o, pos, mass)
+    for theta in (0.5, 0.75):
+        g = _rel(to_np(m.walk(t, theta, eps, n_group=32)).astype(np.float64)[tg], ref)
+        w = _rel(oracle.tree_walk(o, pos, mass, M, com, quad, tg, theta, eps), ref)
+        assert np.median(g) <= 1.5 * np.median(w) + 1e-6, (theta, np.median(g), np.median(w))
+        gm = _rel(to_np(m.walk(t, theta, eps, n_group=32, use_quad=False)).astype(np.float64)[tg], ref)
+        assert np.median(g) < np.median(gm)
+
+
+def test_walk_arguments():
+    m = tb()
+    pos, mass = plummer(3000, 44)
+    p = torch.from_numpy(pos).cuda()
+    t = m.build(p, None, n_crit=16)
+    with pytest.raises(m.TbError) as ei:
+        m.walk(t, 0.5, 1e-3)                                # moments not computed yet
+    assert ei.value.name == "TB_EINVAL"
+    m.moments(t, p, None)
+    for bad in (dict(theta=float("nan")), dict(theta=-1.0), dict(n_group=0)):
+        kw = dict(theta=0.5, eps=1e-3, n_group=32)
+        kw.update(bad)
+        with pytest.raises(m.TbError):
+            m.walk(t, kw["theta"], kw["eps"], n_group=kw["n_group"])
+    a = m.walk(t, 0.5, 1e-3)
+    assert a.shape == (3000, 3) and torch.isfinite(a).all()
+    # a rebuild invalidates the moments until tb_moments runs again
+    m.build(p, None, n_crit=8, tree=t)
+    with pytest.raises(m.TbError):
+        m.walk(t, 0.5, 1e-3)
