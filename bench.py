@@ -45,7 +45,7 @@ from synth import WORKLOADS, batched_plummer, workload  # noqa: E402
 NCU_TRAFFIC = {
     # onesweep pass <8, 512, 8>, N = 2^25 clustered, passes 2 and 3 of a timed
     # build: dram__bytes_read.sum + dram__bytes_write.sum, mean of the two
-    "fb26802ac49effb8": {"bytes": 770.81e6, "n": 1 << 25, "variant": (8, 512, 8)},
+    "6ada3746be75a677": {"bytes": 770.81e6, "n": 1 << 25, "variant": (8, 512, 8)},
 }
 
 METRIC = "tree-build Mparticles/s + HBM roofline %; batched vs plain on same GB300"
@@ -73,6 +73,7 @@ def args_():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reorder", action="store_true", help="skip the key-ordered-input build")
+    ap.add_argument("--no-walk", action="store_true", help="skip the tree-walk timing")
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--precision", action="store_true",
                     help="print the per-level moment error of the three modes against the oracle")
@@ -91,7 +92,7 @@ def peaks():
 
 def kernel_digest():
     h = hashlib.sha256()
-    for f in ("tb_sort.cu", "tb_device.cuh", "tb_internal.h"):
+    for f in ("tb_sort.cu", "tb_device.cuh"):
         with open(os.path.join(ROOT, "paper_2312_06102_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -404,6 +405,12 @@ def run_ours(a):
         tree2.free()
         del pr, wr
 
+    if not a.no_walk and world == 1:
+        try:
+            out["walk"] = run_walk(a, tb, torch)
+        except Exception as ex:  # reported, never hides the main line
+            out["walk"] = {"error": str(ex)[:200]}
+
     if not a.no_batched and world == 1:
         try:
             out["batched"] = run_batched(a, tb, torch)
@@ -468,6 +475,35 @@ class Jitter:
             h3 = _splitmix(h2 ^ ((self.local << 2) | ax))
             u = _srl(h3, 40).to(t.float32) * (2.0 ** -24)
             out[:, ax] = self.base[:, ax] + (2.0 * u - 1.0) * self.amp
+
+
+def run_walk(a, tb, torch):
+    """Gravity from the tree (tb_walk) on a Plummer sphere of 2^22 particles:
+    theta 0.75 and n_crit 10 as in the paper's runs, groups of up to 32,
+    quadrupoles on, softening 1e-3 of the root side."""
+    n = 1 << 22
+    pos, mass = workload("plummer", n, 7)
+    p = torch.from_numpy(pos).cuda()
+    w = torch.from_numpy(mass).cuda()
+    t = tb.build(p, w, n_crit=10)
+    tb.moments(t, p, w)
+    eps = 1e-3 * t.side
+    acc = tb.walk(t, 0.75, eps, n_group=32)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        tb.walk(t, 0.75, eps, n_group=32, out=acc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ok = t.sync() == 0 and bool(torch.isfinite(acc).all())
+    t.free()
+    return {"workload": "plummer n=2^22 (seed 7)", "theta": 0.75, "n_crit": 10, "n_group": 32,
+            "quadrupole": True, "ms": round(ms, 3), "mparticles_s": round(n / (ms / 1e3) / 1e6, 2),
+            "finite": ok}
 
 
 def run_batched(a, tb, torch):
