@@ -54,6 +54,12 @@ def lib():
         L.ora_root.restype = C.c_int
         L.ora_keys.argtypes = [vp, i64, vp, vp, vp]
         L.ora_keys.restype = C.c_int
+        L.ora_keys_ordered.argtypes = [vp, i64, vp, vp, vp, C.c_int]
+        L.ora_keys_ordered.restype = C.c_int
+        L.ora_hilbert.argtypes = [C.c_uint32] * 3
+        L.ora_hilbert.restype = u64
+        L.ora_build_ordered.argtypes = [vp, i64, i32, C.c_int]
+        L.ora_build_ordered.restype = vp
         L.ora_sort.argtypes = [vp, i64, vp, vp]
         L.ora_sort.restype = None
         L.ora_build.argtypes = [vp, i64, i32]
@@ -98,14 +104,23 @@ def quantise(x: float, lo: float, scale: float) -> int:
     return int(lib().ora_quantise(x, lo, scale))
 
 
-def keys(pos):
-    """(keys uint64[n], lo float64[3], side) of the tight root cell (Sec. 2.2)."""
+ORDERS = {"morton": 0, "hilbert": 1}
+
+
+def hilbert(qx: int, qy: int, qz: int) -> int:
+    """Peano-Hilbert key of three 21-bit integers (Sec. 2.2 footnote)."""
+    return int(lib().ora_hilbert(qx, qy, qz))
+
+
+def keys(pos, order: str = "morton"):
+    """(keys uint64[n], lo float64[3], side) of the tight root cell (Sec. 2.2),
+    in Morton or Peano-Hilbert order."""
     pos = _f32pos(pos)
     n = pos.shape[0]
     out = np.empty(n, dtype=np.uint64)
     lo = np.zeros(3)
     side = np.zeros(1)
-    st = lib().ora_keys(_p(pos), n, _p(lo), _p(side), _p(out))
+    st = lib().ora_keys_ordered(_p(pos), n, _p(lo), _p(side), _p(out), ORDERS[order])
     if st:
         raise ValueError("non-finite coordinate")
     return out, lo, float(side[0])
@@ -159,11 +174,12 @@ class _Handle:
             pass
 
 
-def build_tree(pos, n_crit: int) -> Tree:
-    """Top-down Barnes-Hut build (Sec. 2.1) over sorted keys; canonical order."""
+def build_tree(pos, n_crit: int, order: str = "morton") -> Tree:
+    """Top-down Barnes-Hut build (Sec. 2.1) over sorted keys; canonical order
+    (level, then key in the chosen order)."""
     pos = _f32pos(pos)
     n = pos.shape[0]
-    h = lib().ora_build(_p(pos), n, int(n_crit))
+    h = lib().ora_build_ordered(_p(pos), n, int(n_crit), ORDERS[order])
     if lib().ora_status(h):
         lib().ora_free(h)
         raise ValueError("non-finite coordinate")
@@ -248,9 +264,9 @@ class PrefixIndex:
     members of a cell by its key prefix, on sizes where the full top-down
     build is too slow for a test."""
 
-    def __init__(self, pos):
+    def __init__(self, pos, order: str = "morton"):
         self.pos = _f32pos(pos)
-        self.keys, self.lo, self.side = keys(self.pos)
+        self.keys, self.lo, self.side = keys(self.pos, order)
         self.order = np.argsort(self.keys, kind="stable")
         self.skeys = self.keys[self.order]
 

@@ -10,6 +10,7 @@
  *
  * What it computes (paper section in brackets):
  *   ora_keys        root cell and 64-bit particle keys          [Sec. 2.2]
+ *   ora_hilbert     Peano-Hilbert key of three 21-bit integers  [Sec. 2.2 footnote]
  *   ora_sort        stable sort of (key, index) pairs            [Sec. 2.3, step 2]
  *   ora_build       Barnes-Hut top-down build: a cell holding more
  *                   than n_crit particles is halved along each axis
@@ -78,6 +79,41 @@ uint64_t ora_interleave(uint32_t qx, uint32_t qy, uint32_t qz)
     return key;
 }
 
+/* Peano-Hilbert key (the alternative order of the footnote in Sec. 2.2):
+ * Skilling's transform of the three 21-bit coordinates (J. Skilling, AIP
+ * Conf. Proc. 707, 381, 2004: "Programming the Hilbert curve") -- undo the
+ * excess work level by level from the top (invert the low bits of the first
+ * axis when an axis has the level's bit set, else exchange the low bits of
+ * the first axis and that axis), then Gray-encode across the axes and
+ * correct by the parity of the last axis -- and the result interleaved like a
+ * Morton key, first axis most significant, below the leading 1 bit.  Keys of
+ * the points of one depth-d cube share their upper 3d + 1 bits, and
+ * consecutive grid points along the key order are face neighbours. */
+uint64_t ora_hilbert(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    uint32_t X[3] = {qx, qy, qz};
+    const uint32_t M = 1u << 20;
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    return ora_interleave(X[0], X[1], X[2]);
+}
+
 /* one coordinate to a 21-bit integer */
 uint32_t ora_quantise(float x, double lo, double scale)
 {
@@ -113,16 +149,23 @@ int ora_root(const float *pos, int64_t n, double lo[3], double *side)
     return 0;
 }
 
-int ora_keys(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys)
+/* keys in Morton order (order 0) or Peano-Hilbert order (order 1) */
+int ora_keys_ordered(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys,
+                     int order)
 {
     if (ora_root(pos, n, lo, side)) return 1;
     double scale = 2097152.0 / *side;
     for (int64_t i = 0; i < n; ++i) {
         uint32_t q[3];
         for (int a = 0; a < 3; ++a) q[a] = ora_quantise(pos[3 * i + a], lo[a], scale);
-        keys[i] = ora_interleave(q[0], q[1], q[2]);
+        keys[i] = order ? ora_hilbert(q[0], q[1], q[2]) : ora_interleave(q[0], q[1], q[2]);
     }
     return 0;
+}
+
+int ora_keys(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys)
+{
+    return ora_keys_ordered(pos, n, lo, side, keys, 0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -221,7 +264,7 @@ static int idx_cmp(const void *pa, const void *pb)
     return 0;
 }
 
-ora_tree *ora_build(const float *pos, int64_t n, int32_t n_crit)
+ora_tree *ora_build_ordered(const float *pos, int64_t n, int32_t n_crit, int key_order)
 {
     ora_tree *t = (ora_tree *)calloc(1, sizeof(ora_tree));
     t->n = n;
@@ -230,7 +273,7 @@ ora_tree *ora_build(const float *pos, int64_t n, int32_t n_crit)
     uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * nn);
     t->skeys = (uint64_t *)malloc(sizeof(uint64_t) * nn);
     t->perm = (int32_t *)malloc(sizeof(int32_t) * nn);
-    t->status = ora_keys(pos, n, t->lo, &t->side, keys);
+    t->status = ora_keys_ordered(pos, n, t->lo, &t->side, keys, key_order);
     ora_sort(keys, n, t->skeys, t->perm);
     free(keys);
 
@@ -281,6 +324,11 @@ ora_tree *ora_build(const float *pos, int64_t n, int32_t n_crit)
     free(rank);
     free(cv.v);
     return t;
+}
+
+ora_tree *ora_build(const float *pos, int64_t n, int32_t n_crit)
+{
+    return ora_build_ordered(pos, n, n_crit, 0);
 }
 
 int64_t ora_n_cells(const ora_tree *t) { return t->n_cells; }
