@@ -74,6 +74,8 @@ def args_():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reorder", action="store_true", help="skip the key-ordered-input build")
     ap.add_argument("--no-walk", action="store_true", help="skip the tree-walk timing")
+    ap.add_argument("--keys", default="morton", choices=["morton", "hilbert"],
+                    help="particle key order of the timed builds")
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--precision", action="store_true",
                     help="print the per-level moment error of the three modes against the oracle")
@@ -231,6 +233,7 @@ def run_ours(a):
     w = hmass.cuda()
     stream = torch.cuda.current_stream()
 
+    ko = 1 if a.keys == "hilbert" else 0
     # pick the radix-sort variant on this workload (untimed), unless one is named
     cfg = None
     tune_ms = None
@@ -244,12 +247,12 @@ def run_ours(a):
         log(f"[bench] autotune: {cfg} " + " ".join(f"{k}:{v:.3f}" for k, v in tune_ms.items()))
     # first build sizes the cell arrays; later builds use that capacity and
     # need no host synchronisation
-    tree = tb.build(p, w, n_crit=n_crit, sort_cfg=cfg)
+    tree = tb.build(p, w, n_crit=n_crit, sort_cfg=cfg, key_order=ko)
     C = tree.n_cells
     tb.moments(tree, p, w)
     torch.cuda.synchronize()
     for _ in range(a.warmup):
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         tb.moments(tree, p, w)
     torch.cuda.synchronize()
     st = tree.sync()
@@ -268,7 +271,7 @@ def run_ours(a):
     torch.cuda.nvtx.range_push("timed")   # lets a profiler keep to the timed steps
     e0.record(stream)
     for _ in range(a.steps):
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         tb.moments(tree, p, w)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
@@ -331,7 +334,7 @@ def run_ours(a):
                                       if tune_ms else None),
                       "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (1.6 GB positions vs 129 MB), no flush",
-                      "mom_mode": "fp32_compensated"},
+                      "mom_mode": "fp32_compensated", "keys": a.keys},
            "roofline": roofline,
            "build_roofline": {"strict_bytes": int(strict),
                               "achieved_gbs": round(strict / build_s / 1e9, 1),
@@ -343,7 +346,7 @@ def run_ours(a):
     # end to end through the C ABI from pinned host buffers
     if not a.no_e2e:
         res = torch.empty(10, dtype=torch.float32).pin_memory()
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         torch.cuda.synchronize()
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -352,7 +355,7 @@ def run_ours(a):
         for _ in range(a.steps):
             p.copy_(hpos, non_blocking=True)
             w.copy_(hmass, non_blocking=True)
-            tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+            tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
             tb.moments(tree, p, w)
             root = torch.cat([tree.mass[:1], tree.com[0], tree.quad[0]])
             res.copy_(root, non_blocking=True)
@@ -370,7 +373,7 @@ def run_ours(a):
     # key-ordered input: what a simulation sees when it reorders its particle
     # arrays every few steps (tb_reorder), so the build's gather is local
     if not a.no_reorder:
-        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree)
+        tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         torch.cuda.synchronize()
         r0 = torch.cuda.Event(enable_timing=True)
         r1 = torch.cuda.Event(enable_timing=True)
@@ -380,16 +383,16 @@ def run_ours(a):
         r1.record(stream)
         torch.cuda.synchronize()
         reorder_ms = r0.elapsed_time(r1)
-        tree2 = tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg)
+        tree2 = tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, key_order=ko)
         tb.moments(tree2, pr, wr)
         torch.cuda.synchronize()
         for _ in range(a.warmup):
-            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2)
+            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2, key_order=ko)
             tb.moments(tree2, pr, wr)
         torch.cuda.synchronize()
         r0.record(stream)
         for _ in range(a.steps):
-            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2)
+            tb.build(pr, wr, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree2, key_order=ko)
             tb.moments(tree2, pr, wr)
         r1.record(stream)
         torch.cuda.synchronize()

@@ -60,6 +60,16 @@ typedef enum {
     TB_MOM_FP64 = 2         /* FP64 accumulation; also fills mass64 / com64 / quad64 */
 } tb_mom_mode;
 
+/* Particle key order (Sec. 2.2 and its footnote).  Either way a key is a
+ * leading 1 bit and 21 octant digits, and the particles of a depth-d cell
+ * share the key's upper 3d + 1 bits, which is all the build relies on; the
+ * cells are the same, ordered within a level by the chosen key.  Peano-Hilbert
+ * keys follow Skilling's transform (AIP Conf. Proc. 707, 381, 2004). */
+typedef enum {
+    TB_KEYS_MORTON = 0,
+    TB_KEYS_HILBERT = 1
+} tb_key_order;
+
 /* Maximum depth: 1 + 3 * 21 = 64 key bits (Sec. 2.2). */
 #define TB_DEPTH_MAX 21
 #define TB_LEVELS 22
@@ -76,7 +86,8 @@ typedef struct {
     int32_t sort_items;      /* 0 = tuned default; else keys per thread of a sort tile
                                 (compiled variants: see tb_sort_variant) */
     int32_t batch_threads;   /* batched build: threads per set, 0 = tuned default */
-    int32_t reserved;
+    int32_t key_order;       /* tb_key_order: TB_KEYS_MORTON (default) or TB_KEYS_HILBERT
+                                (tb_build only; tb_build_batched takes Morton keys) */
 } tb_params;
 
 /* Host-side description of a tree.  Scalars are valid after a build with

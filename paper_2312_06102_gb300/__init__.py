@@ -13,6 +13,8 @@ importing the binding without the library raises.
 from __future__ import annotations
 
 from ._lib import (  # noqa: F401
+    KEYS_HILBERT,
+    KEYS_MORTON,
     LEVELS,
     MOM_FP32_COMP,
     MOM_FP32_PLAIN,

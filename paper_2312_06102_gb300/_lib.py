@@ -26,7 +26,7 @@ class TbError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("n_crit", C.c_int32), ("mom_mode", C.c_int32), ("cell_capacity", C.c_int64),
                 ("reorder", C.c_int32), ("radix_bits", C.c_int32), ("sort_threads", C.c_int32),
-                ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("reserved", C.c_int32)]
+                ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("key_order", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -242,11 +242,16 @@ def _check(code, what):
         raise TbError(int(code), what)
 
 
+KEYS_MORTON, KEYS_HILBERT = 0, 1
+
+
 def build(pos: torch.Tensor, mass: torch.Tensor | None = None, n_crit: int = 16,
           mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0, reorder: bool = False,
-          radix_bits: int = 0, tree: Tree | None = None, stream=None, sort_cfg=None) -> Tree:
+          radix_bits: int = 0, tree: Tree | None = None, stream=None, sort_cfg=None,
+          key_order: int = KEYS_MORTON) -> Tree:
     """tb_build on a [n,3] float32 CUDA tensor; returns (or rebuilds) a Tree.
-    sort_cfg = (radix_bits, threads, items) picks a compiled sort variant."""
+    sort_cfg = (radix_bits, threads, items) picks a compiled sort variant;
+    key_order is KEYS_MORTON or KEYS_HILBERT."""
     if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3:
         raise ValueError("pos must be a [n,3] float32 tensor")
     t = tree if tree is not None else Tree()
@@ -254,6 +259,7 @@ def build(pos: torch.Tensor, mass: torch.Tensor | None = None, n_crit: int = 16,
         from . import autotune
         sort_cfg = autotune.cached(pos.shape[0])
     p = _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, 0, sort_cfg)
+    p.key_order = int(key_order)
     code = lib().tb_build(_ptr(pos), _ptr(mass), pos.shape[0], C.byref(p), _stream(stream),
                           C.byref(t._p))
     _check(code, "tb_build")
@@ -269,12 +275,13 @@ def moments(tree: Tree, pos: torch.Tensor, mass: torch.Tensor | None = None, str
 def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: torch.Tensor,
                   n_crit: int = 16, mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0,
                   radix_bits: int = 0, batch_threads: int = 0, tree: Tree | None = None,
-                  n_total: int | None = None, stream=None) -> Tree:
+                  n_total: int | None = None, stream=None, key_order: int = KEYS_MORTON) -> Tree:
     """tb_build_batched: set s holds pos[set_offsets[s]:set_offsets[s+1]]."""
     if set_offsets.dtype != torch.int64 or not set_offsets.is_cuda:
         raise ValueError("set_offsets must be an int64 CUDA tensor")
     t = tree if tree is not None else Tree()
     p = _params(n_crit, mom_mode, cell_capacity, 0, radix_bits, batch_threads)
+    p.key_order = int(key_order)
     n_total = pos.shape[0] if n_total is None else n_total
     code = lib().tb_build_batched(_ptr(pos), _ptr(mass), _ptr(set_offsets),
                                   set_offsets.shape[0] - 1, int(n_total), C.byref(p),

@@ -191,6 +191,7 @@ bool valid_params(const tb_params *p) {
     return p && p->n_crit >= 1 && p->n_crit <= kMaxNcrit && p->mom_mode >= 0 && p->mom_mode <= 2 &&
            p->cell_capacity >= 0 &&
            (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11)) &&
+           (p->key_order == TB_KEYS_MORTON || p->key_order == TB_KEYS_HILBERT) &&
            sort_cfg_valid(pick_cfg(p));
 }
 
@@ -299,7 +300,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     uint64_t *kb = (passes & 1) ? t.pkey : ws.keys_alt;
     int32_t *pa = (passes & 1) ? ws.perm_alt : t.perm;
     int32_t *pb = (passes & 1) ? t.perm : ws.perm_alt;
-    e = launch_keys(d_pos, d_mass, n, ka, ws, cfg, s);
+    e = launch_keys(d_pos, d_mass, n, ka, ws, cfg, params->key_order, s);
     if (e != cudaSuccess) return from_cuda(e);
     ws.xm_pos = d_pos;
     ws.xm_mass = d_mass;
@@ -377,6 +378,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
                            tb_stream stream, tb_tree **tree) {
     if (!tree || !valid_params(params) || n_sets < 0 || n_total < 0 || n_total > 2147483647LL)
         return TB_EINVAL;
+    if (params->key_order != TB_KEYS_MORTON) return TB_EINVAL;   // batched: Morton keys only
     if (n_sets > 0 && !d_set_offsets) return TB_EINVAL;
     if (n_total > 0 && (!d_pos || (reinterpret_cast<uintptr_t>(d_pos) & 3u))) return TB_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_mass) & 3u) return TB_EINVAL;

@@ -44,6 +44,37 @@ __device__ __forceinline__ uint64_t morton_key(uint32_t qx, uint32_t qy, uint32_
     return (1ull << 63) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
 }
 
+// Peano-Hilbert key (the alternative order of the footnote in Sec. 2.2):
+// Skilling's transform of the coordinates (J. Skilling, AIP Conf. Proc. 707,
+// 381, 2004) -- from the top level down, an axis whose bit is set inverts the
+// lower bits of the first axis, any other axis swaps its lower bits with the
+// first axis's; then a Gray code across the axes and a correction by the
+// parity of the last axis -- interleaved like a Morton key.  The points of a
+// depth-d cube keep a common key prefix, so the whole pipeline takes these
+// keys unchanged.
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t x, uint32_t y, uint32_t z) {
+#pragma unroll
+    for (int lev = 20; lev >= 1; --lev) {
+        const uint32_t Q = 1u << lev, P = Q - 1;
+        x ^= (x & Q) ? P : 0u;
+        const uint32_t ty = (x ^ y) & P;
+        const bool by = (y & Q) != 0u;
+        x ^= by ? P : ty;
+        y ^= by ? 0u : ty;
+        const uint32_t tz = (x ^ z) & P;
+        const bool bz = (z & Q) != 0u;
+        x ^= bz ? P : tz;
+        z ^= bz ? 0u : tz;
+    }
+    y ^= x;
+    z ^= y;
+    uint32_t t = 0;
+#pragma unroll
+    for (int lev = 20; lev >= 1; --lev)
+        if (z & (1u << lev)) t ^= (1u << lev) - 1u;
+    return morton_key(x ^ t, y ^ t, z ^ t);
+}
+
 // Exact error-free sum a + b = s + e (Knuth's TwoSum, no branch).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);

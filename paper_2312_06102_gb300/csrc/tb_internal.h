@@ -119,7 +119,7 @@ extern int64_t g_launches;
 
 cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len, cudaStream_t s);
 cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
-                        Workspace &ws, const SortCfg &cfg, cudaStream_t s);
+                        Workspace &ws, const SortCfg &cfg, int key_order, cudaStream_t s);
 cudaError_t launch_pack(const float *pos, const float *mass, int64_t n, float4 *xm,
                         cudaStream_t s);
 cudaError_t launch_sort(uint64_t *keys_in_place_a, uint64_t *keys_b, int32_t *perm_a,

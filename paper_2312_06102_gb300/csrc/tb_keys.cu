@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
     }
 }
 
-template <int RADIX_BITS>
+template <int RADIX_BITS, bool HILBERT>
 __global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restrict__ pos,
                                                             const float *__restrict__ mass,
                                                             float m_eq, int64_t n, bool vec,
@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restr
             atomicAdd(&s_hist[p * RADIX + (int)((k >> (shift0 + p * RADIX_BITS)) & (RADIX - 1))], 1u);
     };
     auto key_of = [&](float x, float y, float z) {
-        return morton_key(quantise(x, lx, shi, slo, sc, exact), quantise(y, ly, shi, slo, sc, exact),
-                          quantise(z, lz, shi, slo, sc, exact));
+        const uint32_t qx = quantise(x, lx, shi, slo, sc, exact), qy = quantise(y, ly, shi, slo, sc, exact),
+                       qz = quantise(z, lz, shi, slo, sc, exact);
+        return HILBERT ? hilbert_key(qx, qy, qz) : morton_key(qx, qy, qz);
     };
 
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -264,7 +265,7 @@ cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len
     return cudaGetLastError();
 }
 
-template <int B>
+template <int B, bool H>
 static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uint64_t *keys,
                              Workspace &ws, int passes, int shift0, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(pos) & 15u) == 0 &&
@@ -274,27 +275,32 @@ static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uin
     size_t smem = sizeof(uint32_t) * passes * (1 << B);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(keys_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(keys_kernel<B, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         attr = true;
     }
     int64_t grid = 152 * 4;
     int64_t need = (n + 4 * kKeysThreads - 1) / (4 * kKeysThreads);
     if (need < grid) grid = need < 1 ? 1 : need;
-    keys_kernel<B><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, mass, m_eq, n, vec, keys, ws.xm,
+    keys_kernel<B, H><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, mass, m_eq, n, vec, keys, ws.xm,
                                                               ws.hist, passes, shift0, ws.info);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
-                        Workspace &ws, const SortCfg &cfg, cudaStream_t s) {
+                        Workspace &ws, const SortCfg &cfg, int key_order, cudaStream_t s) {
     const SortPlan plan = sort_plan(cfg);
     const int passes = plan.passes, shift0 = plan.shift0;
+    const bool h = key_order == TB_KEYS_HILBERT;
     switch (cfg.radix_bits) {
-        case 8: return keys_impl<8>(pos, mass, n, keys, ws, passes, shift0, s);
-        case 9: return keys_impl<9>(pos, mass, n, keys, ws, passes, shift0, s);
-        case 10: return keys_impl<10>(pos, mass, n, keys, ws, passes, shift0, s);
-        case 11: return keys_impl<11>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 8: return h ? keys_impl<8, true>(pos, mass, n, keys, ws, passes, shift0, s)
+                         : keys_impl<8, false>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 9: return h ? keys_impl<9, true>(pos, mass, n, keys, ws, passes, shift0, s)
+                         : keys_impl<9, false>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 10: return h ? keys_impl<10, true>(pos, mass, n, keys, ws, passes, shift0, s)
+                          : keys_impl<10, false>(pos, mass, n, keys, ws, passes, shift0, s);
+        case 11: return h ? keys_impl<11, true>(pos, mass, n, keys, ws, passes, shift0, s)
+                          : keys_impl<11, false>(pos, mass, n, keys, ws, passes, shift0, s);
         default: return cudaErrorInvalidValue;
     }
 }

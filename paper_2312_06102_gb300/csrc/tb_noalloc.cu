@@ -128,7 +128,8 @@ extern "C" tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint6
     uint64_t *kb = (passes & 1) ? d_pkey : ws.keys_alt;
     int32_t *pa = (passes & 1) ? ws.perm_alt : d_perm;
     int32_t *pb = (passes & 1) ? d_perm : ws.perm_alt;
-    if ((e = launch_keys(d_pos, nullptr, n, ka, ws, cfg, s)) != cudaSuccess) return status_of(e);
+    if ((e = launch_keys(d_pos, nullptr, n, ka, ws, cfg, TB_KEYS_MORTON, s)) != cudaSuccess)
+        return status_of(e);
     uint64_t *kout = nullptr;
     int32_t *pout = nullptr;
     if ((e = launch_sort(ka, kb, pa, pb, n, ws, cfg, kout, pout, s)) != cudaSuccess)
