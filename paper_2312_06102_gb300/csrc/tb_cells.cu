@@ -328,6 +328,151 @@ __global__ void __launch_bounds__(kLvThreads, 2)
     emit_particle(f, P, 0, n, Kpre, out);
 }
 
+// Emission over the leaf starts only, two count tiles (2048 particles) per
+// block.  Only a leaf start (m_k <= L_k) opens or closes cells, about one
+// particle in seven, so the block first lists them in order in shared memory
+// (four particles per thread, a block-wide prefix of the counts) and then
+// runs the per-level prefix and the writes over that list, 32 starts per
+// warp: every lane holds a start, and the level masks are built for the
+// list, not for every particle.  The tree's last particle, which closes every
+// cell that holds it, is handled by its own thread: those are the last cells
+// of their levels.
+constexpr int kEfThreads = 512;
+constexpr int kEfWarps = kEfThreads / 32;
+constexpr int kEfTile = 2 * kLvTile;
+constexpr int kEfChunks = kEfTile / 32;
+
+__global__ void __launch_bounds__(kEfThreads, 2)
+    emit_starts_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
+                       const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
+                       EmitOut out) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    __shared__ uint32_t s_entry[kEfTile];               // k - s | m << 11 | L << 16 | Lprev << 21
+    __shared__ uint32_t s_mask[kEfChunks][kLevels];     // level masks of each chunk of 32 starts
+    __shared__ uint32_t s_cpre[kEfChunks][kLevels];     // starts of each level in earlier chunks
+    __shared__ uint32_t s_base[kLevelFields];           // first level-d cell (leaf) of the block
+    __shared__ uint32_t s_wcnt[kEfWarps];
+    __shared__ uint8_t s_Llast[kEfThreads];
+    __shared__ uint32_t s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t0 = 2 * (int64_t)blockIdx.x;          // first count tile of the block
+    const int64_t s = (int64_t)blockIdx.x * kEfTile, e = min64(n, s + kEfTile);
+    if (threadIdx.x < kLevelFields)
+        s_base[threadIdx.x] = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
+                              tile_off[(int64_t)threadIdx.x * n_tiles + t0];
+    // m and L of four particles per thread
+    const int64_t k0 = s + 4 * (int64_t)threadIdx.x;
+    uint32_t m[4], L[4];
+    if (k0 + 4 <= e) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(ml + k0);
+        m[0] = v.x & 0xffu; L[0] = (v.x >> 8) & 0xffu; m[1] = (v.x >> 16) & 0xffu; L[1] = v.x >> 24;
+        m[2] = v.y & 0xffu; L[2] = (v.y >> 8) & 0xffu; m[3] = (v.y >> 16) & 0xffu; L[3] = v.y >> 24;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t v = (k0 + j < e) ? (uint32_t)ml[k0 + j] : 255u;
+            m[j] = v & 0xffu;
+            L[j] = (k0 + j < e) ? (v >> 8) : 0u;
+        }
+    }
+    s_Llast[threadIdx.x] = (uint8_t)L[3];
+    uint32_t Lbefore = 0;
+    if (threadIdx.x == 0 && s > 0) Lbefore = (uint32_t)(ml[s - 1] >> 8);
+    // the tree's last particle closes the cells holding it: the last cell of
+    // each level 0 .. L, whose children end where the next level ends
+    if (k0 <= n - 1 && n - 1 < k0 + 4) {
+        const uint32_t Ll = L[(int)(n - 1 - k0)];
+        for (int d = 0; d <= (int)Ll; ++d) {
+            const int64_t idx = info->level_offset[d + 1] - 1;
+            out.pend[idx] = (int32_t)n;
+            out.child_end[idx] = (d < (int)Ll) ? (int32_t)info->level_offset[d + 2] : -1;
+        }
+    }
+    __syncthreads();
+    const uint32_t Lp0 = threadIdx.x > 0 ? (uint32_t)s_Llast[threadIdx.x - 1] : Lbefore;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cnt += (m[j] <= L[j]) ? 1u : 0u;
+    uint32_t x = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_wcnt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = 0;
+        for (int w = 0; w < kEfWarps; ++w) { const uint32_t c = s_wcnt[w]; s_wcnt[w] = r; r += c; }
+        s_total = r;
+    }
+    __syncthreads();
+    uint32_t pos = s_wcnt[warp] + x - cnt;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (m[j] <= L[j]) {
+            const uint32_t lp = j ? L[j - 1] : Lp0;
+            s_entry[pos++] = (uint32_t)(4 * threadIdx.x + j) | (m[j] << 11) | (L[j] << 16) | (lp << 21);
+        }
+    }
+    __syncthreads();
+    const int total = (int)s_total;
+    const int nchunks = (total + 31) / 32;
+    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose)
+    for (int c = warp; c < nchunks; c += kEfWarps) {
+        const int i = c * 32 + lane;
+        uint32_t v = 0;
+        if (i < total) {
+            const uint32_t en = s_entry[i];
+            const uint32_t mm = (en >> 11) & 31u, LL = (en >> 16) & 31u;
+            v = (2u << LL) - (1u << mm);
+        }
+        uint32_t msk = 0x0000ffffu;
+#pragma unroll
+        for (int j = 16; j > 0; j >>= 1, msk ^= msk << j) {
+            const uint32_t y = __shfl_xor_sync(0xffffffffu, v, j);
+            if (lane & j) v ^= ((y >> j) ^ v) & msk;
+            else v ^= (((v >> j) ^ y) & msk) << j;
+        }
+        if (lane < kLevels) s_mask[c][lane] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels) {
+        uint32_t r = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            s_cpre[c][threadIdx.x] = r;
+            r += __popc(s_mask[c][threadIdx.x]);
+        }
+    }
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    for (int c = warp; c < nchunks; c += kEfWarps) {
+        const int i = c * 32 + lane;
+        if (i >= total) continue;
+        const uint32_t en = s_entry[i];
+        const int64_t k = s + (en & 2047u);
+        const int mm = (int)((en >> 11) & 31u), LL = (int)((en >> 16) & 31u), Lp = (int)((en >> 21) & 31u);
+        auto P = [&](int d) { return s_base[d] + s_cpre[c][d] + (uint32_t)__popc(s_mask[c][d] & lt); };
+        const uint64_t K = skeys[k];
+        if (k > 0) {
+            // close the cells holding k-1 but not k
+            for (int d = mm; d <= Lp; ++d) {
+                const uint32_t idx = P(d) - 1;
+                out.pend[idx] = (int32_t)k;
+                out.child_end[idx] = (d < Lp) ? (int32_t)P(d + 1) : -1;
+            }
+        }
+        for (int d = mm; d <= LL; ++d) {
+            const uint32_t idx = P(d);
+            out.ckey[idx] = cell_key(K, d);
+            out.level[idx] = (uint8_t)d;
+            out.pfirst[idx] = (int32_t)k;
+            out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == mm ? 1 : 0);
+            out.child_first[idx] = (d < LL) ? (int32_t)P(d + 1) : -1;
+        }
+        out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)P(LL);
+    }
+}
+
 }  // namespace
 
 int level_tile_size() { return kLvTile; }
@@ -376,8 +521,9 @@ cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int ncrit, Workspace &
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
     EmitOut o{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
               t.leaf_cell};
-    emit_kernel<<<(unsigned)tiles, kLvThreads, 0, s>>>(skeys, ws.ml, n, ws.level_cnt, tiles,
-                                                       ws.info, o);
+    const int64_t blocks = (n + kEfTile - 1) / kEfTile;
+    emit_starts_kernel<<<(unsigned)blocks, kEfThreads, 0, s>>>(skeys, ws.ml, n, ws.level_cnt, tiles,
+                                                               ws.info, o);
     ++g_launches;
     return cudaGetLastError();
 }
