@@ -80,6 +80,38 @@ __global__ void __launch_bounds__(kMomThreads, 3)
     }
 }
 
+// Compensated mode: every leaf of at most kSplitLeaf members, in key order,
+// with the split sums only (few registers, many warps in flight); longer
+// leaves are queued for mid_leaf_kernel (compensated sums) or, beyond
+// kBigLeafThread, for big_leaf_kernel.
+__global__ void __launch_bounds__(kMomThreads, 4)
+    leaf_split_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell,
+                      const float4 *__restrict__ xs, int32_t *mid_queue, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    const int64_t nl = info->n_leaves;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
+        const int64_t c = leaf_cell[j];
+        const int64_t pf = T.pfirst[c], pe = T.pend[c];
+        if (pe - pf > kBigLeafThread) T.big_leaf[atomicAdd(&info->misc_ctr[2], 1u)] = (int32_t)c;
+        else if (pe - pf > kSplitLeaf) mid_queue[atomicAdd(&info->misc_ctr[5], 1u)] = (int32_t)c;
+        else leaf_sum_split(o, xs, c, pf, pe);
+    }
+}
+
+// Compensated mode: the queued leaves of kSplitLeaf + 1 .. kBigLeafThread members.
+__global__ void __launch_bounds__(kMomThreads, 3)
+    mid_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, const int32_t *mid_queue,
+                    DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    const int64_t nq = *(volatile const uint32_t *)&info->misc_ctr[5];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const int64_t c = mid_queue[q];
+        leaf_sum<TB_MOM_FP32_COMP>(o, xs, c, T.pfirst[c], T.pend[c]);
+    }
+}
+
 // The non-leaf cells of level d, from their children (finished by the
 // launch for level d + 1, or by the leaf launches).  Each warp takes 64
 // consecutive cells and packs their non-leaf ones, in order, onto its lanes.
@@ -241,7 +273,8 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
     const int64_t n = t.n_particles;
-    cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 2 * sizeof(uint32_t), s);
+    // misc_ctr[2..3]: big-leaf queue and tickets; [5]: mid-leaf queue
+    cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int64_t g = (n / 4 + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -254,9 +287,23 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     int64_t grid = (n + kMomThreads - 1) / kMomThreads;
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
-    leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs, ws.info);
-    ++g_launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if constexpr (MODE == TB_MOM_FP32_COMP) {
+        // the mid-leaf queue (at most n / 17 leaves) sits in the upper half
+        // of the big-leaf buffer (at most n / 2049 entries in the lower)
+        int32_t *mid = ws.big_leaf + (n + 1) / 2;
+        leaf_split_kernel<<<(unsigned)(152 * 8), kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs, mid,
+                                                                     ws.info);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        mid_leaf_kernel<<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xs, mid, ws.info);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs,
+                                                                         ws.info);
+        ++g_launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xs, ws.info);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -268,6 +268,40 @@ __device__ void finish_split(const MomOut &o, int64_t c, const AccP &A, const Ac
     write_cell_f32(o, c, M, ch, cl, Q, bb);
 }
 
+// A leaf of at most kSplitLeaf members in the compensated mode: two
+// interleaved plain FP32 accumulators (see kSplitLeaf).
+__device__ __forceinline__ void leaf_sum_split(const MomOut &o, const float4 *__restrict__ xs, int64_t c,
+                                               int64_t pf, int64_t pe) {
+    constexpr int G = 4;
+    const float4 r0 = xs[pf];
+    const float ref[3] = {r0.x, r0.y, r0.z};
+    float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+    AccP A, B;
+    A.init();
+    B.init();
+    for (int64_t k0 = pf; k0 < pe; k0 += G) {
+        const int cnt = (int)min64(G, pe - k0);
+        float4 v[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (j < cnt) v[j] = xs[k0 + j];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (j >= cnt) break;
+            const float x[3] = {v[j].x, v[j].y, v[j].z};
+            for (int a = 0; a < 3; ++a) {
+                bb[a] = fminf(bb[a], x[a]);
+                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            }
+            const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
+                                 __fsub_rn(x[2], ref[2])};
+            if (j & 1) B.add(v[j].w, dx);
+            else A.add(v[j].w, dx);
+        }
+    }
+    finish_split(o, c, A, B, ref, bb);
+}
+
 // Sum the members [pf, pe) of one leaf from the key-ordered records; loads
 // are issued four at a time before any is used.  Leaves reaching this path
 // hold at most 2048 particles (longer ones, only possible at depth 21, go to
@@ -281,30 +315,7 @@ __device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t
     float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
     if constexpr (MODE == TB_MOM_FP32_COMP) {
         if (pe - pf <= kSplitLeaf) {
-            AccP A, B;
-            A.init();
-            B.init();
-            for (int64_t k0 = pf; k0 < pe; k0 += G) {
-                const int cnt = (int)min64(G, pe - k0);
-                float4 v[G];
-#pragma unroll
-                for (int j = 0; j < G; ++j)
-                    if (j < cnt) v[j] = xs[k0 + j];
-#pragma unroll
-                for (int j = 0; j < G; ++j) {
-                    if (j >= cnt) break;
-                    const float x[3] = {v[j].x, v[j].y, v[j].z};
-                    for (int a = 0; a < 3; ++a) {
-                        bb[a] = fminf(bb[a], x[a]);
-                        bb[3 + a] = fmaxf(bb[3 + a], x[a]);
-                    }
-                    const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
-                                         __fsub_rn(x[2], ref[2])};
-                    if (j & 1) B.add(v[j].w, dx);
-                    else A.add(v[j].w, dx);
-                }
-            }
-            finish_split(o, c, A, B, ref, bb);
+            leaf_sum_split(o, xs, c, pf, pe);
             return;
         }
     }
