@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
     if (vec) {
         const float4 *p4 = reinterpret_cast<const float4 *>(pos);
         const int64_t groups = n / 4;
+#pragma unroll 2
         for (int64_t g = tid; g < groups; g += stride) {
             float4 a = __ldcs(p4 + 3 * g), c = __ldcs(p4 + 3 * g + 1), d = __ldcs(p4 + 3 * g + 2);
             b.add(a.x, 0); b.add(a.y, 1); b.add(a.z, 2); b.add(a.w, 0);
@@ -97,15 +98,40 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
     __threadfence();
 
     // last block: combine the per-block partials and derive the root cube
-    if (threadIdx.x < 7) {
-        float v = __ldcg(&part[threadIdx.x]);
-        for (unsigned k = 1; k < gridDim.x; ++k) {
-            float u = __ldcg(&part[k * 8 + threadIdx.x]);
-            if (threadIdx.x < 3) v = fminf(v, u);
-            else if (threadIdx.x < 6) v = fmaxf(v, u);
-            else v = __uint_as_float(__float_as_uint(v) | __float_as_uint(u));
+    // every thread folds a stride of the partials, then the block reduces
+    {
+        Box c;
+        c.init();
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+            const float4 lo = __ldcg(reinterpret_cast<const float4 *>(part + 8 * k));
+            const float4 hi = __ldcg(reinterpret_cast<const float4 *>(part + 8 * k + 4));
+            c.mn[0] = fminf(c.mn[0], lo.x); c.mn[1] = fminf(c.mn[1], lo.y); c.mn[2] = fminf(c.mn[2], lo.z);
+            c.mx[0] = fmaxf(c.mx[0], lo.w); c.mx[1] = fmaxf(c.mx[1], hi.x); c.mx[2] = fmaxf(c.mx[2], hi.y);
+            c.bad |= __float_as_uint(hi.z);
         }
-        s_red[0][threadIdx.x] = v;
+        for (int off = 16; off > 0; off >>= 1) {
+            for (int a = 0; a < 3; ++a) {
+                c.mn[a] = fminf(c.mn[a], __shfl_xor_sync(0xffffffffu, c.mn[a], off));
+                c.mx[a] = fmaxf(c.mx[a], __shfl_xor_sync(0xffffffffu, c.mx[a], off));
+            }
+            c.bad |= __shfl_xor_sync(0xffffffffu, c.bad, off);
+        }
+        __syncthreads();   // s_red's block partials were read above
+        if (lane == 0) {
+            for (int a = 0; a < 3; ++a) { s_red[warp][a] = c.mn[a]; s_red[warp][3 + a] = c.mx[a]; }
+            s_red[warp][6] = __uint_as_float(c.bad);
+        }
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            float v = s_red[0][threadIdx.x];
+            for (int w = 1; w < kRootThreads / 32; ++w) {
+                const float u = s_red[w][threadIdx.x];
+                if (threadIdx.x < 3) v = fminf(v, u);
+                else if (threadIdx.x < 6) v = fmaxf(v, u);
+                else v = __uint_as_float(__float_as_uint(v) | __float_as_uint(u));
+            }
+            s_red[0][threadIdx.x] = v;
+        }
     }
     for (int i = threadIdx.x; i < hist_len; i += blockDim.x) hist[i] = 0;
     __syncthreads();
