@@ -45,7 +45,7 @@ struct SortSmem {
 };
 
 template <int RADIX_BITS, int THREADS, int ITEMS, bool FIRST>
-__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 3 : 2) : (ITEMS <= 8 ? 2 : 1)))
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 4 : 2) : (ITEMS <= 8 ? 2 : 1)))
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out, int64_t n,
                     int pass, int shift0, const uint32_t *__restrict__ digit_off, uint64_t *lookback,
