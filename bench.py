@@ -176,6 +176,19 @@ def oracle_rate(pos, mass, n_crit, sample):
     return m / dt / 1e6, dt, m
 
 
+def whole_job_rate(n_per_rank, steps, world, ms, device="cuda"):
+    """The slowest rank's time for `steps` builds (max over ranks) and the
+    whole-job rate: the particles all ranks built / that time, Mparticles/s.
+    Each rank builds its own replica; nothing but this maximum is exchanged."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, n_per_rank * steps * world / (ms / 1e3) / 1e6
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -285,11 +298,7 @@ def run_ours(a):
     st = tree.sync()
     if st != 0:
         raise SystemExit(f"timed build failed: {tb.STATUS[st]}")
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * a.steps * world / (ms / 1e3) / 1e6
+    ms, value = whole_job_rate(n, a.steps, world, ms)
 
     # per-stage totals over the timed region
     agg = {}
@@ -362,11 +371,8 @@ def run_ours(a):
         f1.record(stream)
         torch.cuda.synchronize()
         ems = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        out["e2e"] = {"value": round(n * a.steps * world / (ems / 1e3) / 1e6, 2),
+        ems, evalue = whole_job_rate(n, a.steps, world, ems)
+        out["e2e"] = {"value": round(evalue, 2),
                       "unit": "Mparticles/s", "h2d_bytes_per_step": int(16 * n),
                       "d2h_bytes_per_step": 40}
 

@@ -25,3 +25,48 @@ def test_metric_names_the_baseline_metric():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     with open(os.path.join(root, "BASELINE.json")) as f:
         assert json.load(f)["metric"] == bench.METRIC
+
+
+def _rate_worker(rank, world, port, q):
+    import os
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, value = bench.whole_job_rate(1000, 4, world, 10.0 * (rank + 1), device="cpu")
+        q.put((rank, ms, value))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_gloo():
+    """world_size 2 on the CPU: both ranks report the slower rank's time and
+    the rate of all ranks' particles over it."""
+    import socket
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rate_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, value in got:
+        assert ms == 20.0
+        assert value == pytest.approx(1000 * 4 * 2 / 0.020 / 1e6)
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
+    """Under torchrun only rank 0 runs the oracle arm; the others exit 0 at once."""
+    import sys
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    a = bench.args_()
+    assert bench.run_reference(a) == 0
+    assert capsys.readouterr().out == ""
