@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kMomThreads, 3)
 // launch for level d + 1, or by the leaf launches).  Each warp takes 64
 // consecutive cells and packs their non-leaf ones, in order, onto its lanes.
 template <int MODE>
-__global__ void __launch_bounds__(kMomThreads, 3)
+__global__ void __launch_bounds__(kMomThreads, 4)
     level_moments_kernel(TreeIn T, MomOut o, DevInfo *info, int d) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     __shared__ int32_t s_list[kMomThreads / 32][64];

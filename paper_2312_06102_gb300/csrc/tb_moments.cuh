@@ -94,6 +94,37 @@ struct AccC {
     }
 };
 
+// Parents in the compensated mode: mass and first moment compensated (their
+// errors would otherwise add up over 21 levels), second moment plain -- a
+// parent's second-moment error relative to M s^2 is at most about 54 u from
+// its own sum and a quarter of each child's (whose side is half), so it stays
+// below 72 u (4.3e-6), under the 1e-5 tolerance, at every level.
+struct AccS {
+    float M, Mc, S[3], Sc[3], Q[6];
+    __device__ void init() {
+        M = Mc = 0.f;
+        for (int a = 0; a < 3; ++a) S[a] = Sc[a] = 0.f;
+        for (int j = 0; j < 6; ++j) Q[j] = 0.f;
+    }
+    // a child of mass m, centre ref + (h + l), central second moment q
+    __device__ void add_cell(float m, const float h[3], const float l[3], const float q[6]) {
+        float e;
+        two_sum(M, m, M, e);
+        Mc += e;
+        float p[3];
+        for (int a = 0; a < 3; ++a) {
+            float pe;
+            two_prod(m, h[a], p[a], pe);
+            pe = __fmaf_rn(m, l[a], pe);
+            two_sum(S[a], p[a], S[a], e);
+            Sc[a] += e + pe;
+        }
+        int j = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b, ++j) Q[j] = __fmaf_rn(p[a], h[b], __fadd_rn(Q[j], q[j]));
+    }
+};
+
 struct AccP {
     float M, S[3], Q[6];
     __device__ void init() {
@@ -208,6 +239,31 @@ __device__ void finish_c(const MomOut &o, int64_t c, const AccC &A, const float 
             two_sum(A.Q[j], -p, qh, ql);
             Q[j] = __fadd_rn(qh, __fadd_rn(ql, __fsub_rn(A.Qc[j], pe)));
         }
+    float ch[3], cl[3];
+    for (int a = 0; a < 3; ++a) {
+        float h, l;
+        two_sum(ref[a], rh[a], h, l);
+        l = __fadd_rn(l, rl[a]);
+        fast_two_sum(h, l, ch[a], cl[a]);
+    }
+    write_cell_f32(o, c, Mh + Ml, ch, cl, Q, bb);
+}
+
+__device__ void finish_s(const MomOut &o, int64_t c, const AccS &A, const float ref[3],
+                         const float bb[6]) {
+    float Mh, Ml;
+    fast_two_sum(A.M, A.Mc, Mh, Ml);
+    float rh[3], rl[3];
+    for (int a = 0; a < 3; ++a) {
+        float sh, sl;
+        fast_two_sum(A.S[a], A.Sc[a], sh, sl);
+        if (Mh != 0.f) df_div(sh, sl, Mh, Ml, rh[a], rl[a]);
+        else rh[a] = rl[a] = 0.f;
+    }
+    float Q[6];
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++j) Q[j] = __fmaf_rn(-__fmul_rn(Mh, rh[a]), rh[b], A.Q[j]);
     float ch[3], cl[3];
     for (int a = 0; a < 3; ++a) {
         float h, l;
@@ -437,7 +493,7 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
             // leaf)
             float ref[3];
             for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
-            AccC A;
+            AccS A;
             A.init();
             for (int32_t c = c0; c < c1; ++c) {
                 float h[3], l[3], q[6], cb[6];
@@ -449,7 +505,7 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
                 }
                 A.add_cell(o.mass[c], h, l, q);
             }
-            finish_c(o, p, A, ref, bb);
+            finish_s(o, p, A, ref, bb);
             return;
         }
     }
