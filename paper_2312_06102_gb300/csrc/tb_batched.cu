@@ -23,6 +23,7 @@
 
 #include "tb_cells.cuh"
 #include "tb_ctasort.cuh"
+#include "tb_runs.cuh"
 #include "tb_moments.cuh"
 
 namespace tb {
@@ -33,7 +34,10 @@ constexpr int kBThreads = kCtaThreads;        // front / emit blocks (one partic
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBRadixBits = kCtaRadixBits;
 constexpr int kBRadix = kCtaRadix;
-constexpr int kBPasses = (63 + kBRadixBits - 1) / kBRadixBits;
+// the block sort orders the upper 40 key bits in five passes; the runs of
+// equal upper bits are then ordered in place (tb_runs.cuh)
+constexpr int kBPasses = 5;
+constexpr int kBShift0 = 63 - kBPasses * kBRadixBits;
 constexpr int kBMomThreads = 256;
 constexpr int kBigLeafSerial = 1 << 20;       // leaves above this are summed in FP64
 
@@ -143,6 +147,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
     __shared__ double s_scale;
     __shared__ bool s_exact;
     __shared__ int s_q;
+    __shared__ int s_nlong;
+    __shared__ int64_t s_long[32];
+    __shared__ unsigned long long s_end;
     for (;;) {
         const int q = take_set(&A.queue[0], A.n_sets, &s_q);
         if (q < 0) return;
@@ -184,23 +191,57 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
             const double sc = s_scale;
             const bool ex = s_exact;
             const float m_eq = (float)(1.0 / (double)ns);
-            // unsorted keys go where pass 0 reads them: kBPasses is even, so the
-            // passes run pkey -> kalt -> ... -> pkey
+            // unsorted keys go where pass 0 reads them: kBPasses is odd, so the
+            // passes run kalt -> pkey -> ... -> pkey
             for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x) {
                 const float x = A.pos[3 * i], y = A.pos[3 * i + 1], z = A.pos[3 * i + 2];
                 const uint64_t k = morton_key(quantise(x, lx, shi, slo, sc, ex),
                                               quantise(y, ly, shi, slo, sc, ex),
                                               quantise(z, lz, shi, slo, sc, ex));
-                A.pkey[i] = k;
+                A.kalt[i] = k;
                 A.xm[i] = make_float4(x, y, z, A.mass ? A.mass[i] : m_eq);
                 for (int p = 0; p < kBPasses; ++p)
-                    atomicAdd(&sm.hist[p][(k >> (p * kBRadixBits)) & (kBRadix - 1)], 1u);
+                    atomicAdd(&sm.hist[p][(k >> (kBShift0 + p * kBRadixBits)) & (kBRadix - 1)], 1u);
             }
         }
         __syncthreads();
-        // ---- stable LSD sort of the set (its digit counts were taken above)
-        cta_lsd_sort(A.pkey, A.perm, A.kalt, A.palt, o, ns, 0, kBPasses, true, sm);
+        // ---- stable LSD sort of the set by its upper key bits (digit counts
+        // taken above), then the runs of equal upper bits by the low bits
+        cta_lsd_sort(A.kalt, A.palt, A.pkey, A.perm, o, ns, kBShift0, kBPasses, true, sm);
         __syncthreads();
+        for (int64_t t0 = o; t0 < o + ns; t0 += kRunTile) {
+            if (threadIdx.x == 0) s_nlong = 0;
+            __syncthreads();
+            run_tile<kBThreads>(A.pkey, A.perm, o, t0, o + ns, kBShift0, *reinterpret_cast<RunSmem *>(raw),
+                                [&](int64_t a) { s_long[atomicAdd(&s_nlong, 1)] = a; });
+            const int nl = s_nlong;
+            for (int j = 0; j < nl; ++j) {
+                // a run of more than kRunMax keys (at most 16 start in a tile):
+                // its end, then the block sort of its low bits
+                const int64_t a = s_long[j];
+                const uint64_t tp = A.pkey[a] >> kBShift0;
+                if (threadIdx.x == 0) s_end = (unsigned long long)(o + ns);
+                __syncthreads();
+                for (int64_t base = a + 1; base < o + ns; base += blockDim.x) {
+                    const int64_t p = base + threadIdx.x;
+                    if (p < o + ns && (A.pkey[p] >> kBShift0) != tp) atomicMin(&s_end, (unsigned long long)p);
+                    __syncthreads();
+                    const bool done = s_end < (unsigned long long)(o + ns);
+                    __syncthreads();
+                    if (done) break;
+                }
+                const int64_t len = (int64_t)s_end - a;
+                constexpr int low_passes = (kBShift0 + kBRadixBits - 1) / kBRadixBits;
+                cta_histograms(A.pkey, a, len, 0, low_passes, sm);
+                const int np = cta_lsd_sort(A.pkey, A.perm, A.kalt, A.palt, a, len, 0, low_passes, false, sm);
+                if (np & 1)
+                    for (int64_t p = a + threadIdx.x; p < a + len; p += blockDim.x) {
+                        A.pkey[p] = A.kalt[p];
+                        A.perm[p] = A.palt[p];
+                    }
+                __syncthreads();
+            }
+        }
         // ---- cells and leaves started per level (the set is its own tree)
         if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] = 0;
         __syncthreads();
