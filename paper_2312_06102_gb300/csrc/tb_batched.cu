@@ -88,9 +88,32 @@ __global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int
         for (int c = 33; c >= 0; --c) { uint32_t v = cls[c]; cls[c] = run; run += v; }
     }
     __syncthreads();
-    // stable within a class: one thread walks the sets in order
-    if (threadIdx.x == 0)
-        for (int s = 0; s < S; ++s) order[cls[klass(s)]++] = s;
+    // stable within a class: chunks of 1024 sets in order; inside a chunk a
+    // set's place is its class's running base, plus the sets of its class in
+    // earlier warps, plus those in earlier lanes of its warp
+    __shared__ uint32_t wc[32][34];
+    __shared__ uint32_t tot[34];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < S; c0 += 1024) {
+        for (int i = threadIdx.x; i < 32 * 34; i += blockDim.x) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        const int s = c0 + (int)threadIdx.x;
+        const int c = s < S ? klass(s) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c >= 0 && lane == __ffs(peers) - 1) wc[warp][c] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 34) {
+            uint32_t r = 0;
+            for (int w = 0; w < 32; ++w) { const uint32_t v = wc[w][threadIdx.x]; wc[w][threadIdx.x] = r; r += v; }
+            tot[threadIdx.x] = r;
+        }
+        __syncthreads();
+        if (c >= 0) order[cls[c] + wc[warp][c] + (uint32_t)__popc(peers & lt)] = s;
+        __syncthreads();
+        if (threadIdx.x < 34) cls[threadIdx.x] += tot[threadIdx.x];
+        __syncthreads();
+    }
 }
 
 __device__ __forceinline__ int take_set(uint32_t *ticket, int32_t S, int *s_q) {
