@@ -18,12 +18,13 @@
 // Canonical order is level-major, key (= first particle) ascending within a
 // level, so the index of cell (d, k) is level_offset[d] + P_d(k), P_d(k) the
 // number of level-d starts before k: a 22-way prefix count, done in three
-// launches over tiles of 1024 particles, one particle per thread:
+// launches over tiles of 1024 particles:
 //   level_count_kernel : per tile, the cells started at each level and the
 //                        leaves started (one warp ballot per level);
 //   level_scan_kernel  : per level, prefix over tiles; the last block forms the
 //                        level offsets, the cell count and the depth;
-//   emit_kernel        : re-derives m and L, and writes every cell.
+//   emit_starts_kernel : reads m and L back, lists the leaf starts, and writes
+//                        every cell.
 // Links follow from the same counts (P_d(k) before k's own starts):
 //   index of (d, k)        = P_d(k);
 //   parent of (d, k)       = (d-1, k) = P_{d-1}(k) if d > m_k, else the level-(d-1)
@@ -282,50 +283,6 @@ __global__ void __launch_bounds__(kScanThreads)
     info->max_depth = dmax;
     if (cell_cap > 0 && off > cell_cap) info->status |= kErrOverflow;
     info->misc_ctr[1] = 0;
-}
-
-__global__ void __launch_bounds__(kLvThreads, 2)
-    emit_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
-                const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
-                EmitOut out) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    __shared__ TileShared ts;
-    __shared__ uint32_t woff[kLvWarps][kLevelFields];
-    __shared__ uint32_t tot[kLevelFields];
-    __shared__ uint8_t s_L[kLvTile];
-    const int64_t t = blockIdx.x;
-    const int64_t s = t * kLvTile, e = min64(n, s + kLvTile);
-    // every global load of the block is issued first, so that their
-    // latencies overlap: m and L from the count pass (and L of the particle
-    // before the tile), the key, and the tile's offsets
-    Front f;
-    f.k = s + threadIdx.x;
-    const bool in = f.k < e;
-    const uint32_t v = in ? (uint32_t)ml[f.k] : 255u;
-    const uint64_t Kpre = in ? skeys[f.k] : 0ull;
-    uint32_t Lbefore = 0;
-    if (threadIdx.x == 0 && f.k > 0) Lbefore = (uint32_t)(ml[f.k - 1] >> 8);
-    uint32_t base_v = 0;
-    if (threadIdx.x < kLevelFields)
-        base_v = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
-                 tile_off[(int64_t)threadIdx.x * n_tiles + t];
-    f.m = v & 255u;
-    f.L = in ? (int)(v >> 8) : 0;
-    s_L[threadIdx.x] = (uint8_t)f.L;
-    const int warp = threadIdx.x >> 5;
-    store_level_masks(f.m, f.L, ts);
-    __syncthreads();
-    warp_field_prefix(ts, woff, tot);
-    if (threadIdx.x < kLevelFields) ts.base[threadIdx.x] = base_v;
-    f.Lprev = (threadIdx.x > 0) ? s_L[threadIdx.x - 1] : (int)Lbefore;
-    __syncthreads();
-    if (f.k >= e) return;
-    const unsigned lt = lanemask_lt();
-    // P_d(k): level-d starts before k, as a global cell index
-    auto P = [&](int d) {
-        return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
-    };
-    emit_particle(f, P, 0, n, Kpre, out);
 }
 
 // Emission over the leaf starts only, two count tiles (2048 particles) per
