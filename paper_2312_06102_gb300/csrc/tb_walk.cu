@@ -50,6 +50,7 @@ struct WalkTree {
     const float4 *xs;               // particles in key order: x, y, z, m
     const int32_t *perm;
     double side;
+    const float4 *rec;              // [C][4] per cell: com + m, com_lo, T xx xy xz yy, T yz zz
 };
 
 struct WarpLists {
@@ -73,16 +74,15 @@ __device__ float3 evaluate(const WalkTree &T, const WarpLists &W, int ncell, int
     const float4 x = k < ke ? T.xs[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int j = 0; j < ncell; ++j) {
         const int c = W.cell[j];
-        const float m = T.mass[c];
-        const float rx = (x.x - T.com[3 * c]) - T.com_lo[3 * c];
-        const float ry = (x.y - T.com[3 * c + 1]) - T.com_lo[3 * c + 1];
-        const float rz = (x.z - T.com[3 * c + 2]) - T.com_lo[3 * c + 2];
+        const float4 c0 = T.rec[4 * c], c1 = T.rec[4 * c + 1];
+        const float m = c0.w;
+        const float rx = (x.x - c0.x) - c1.x;
+        const float ry = (x.y - c0.y) - c1.y;
+        const float rz = (x.z - c0.z) - c1.z;
         a = point_acc(a, rx, ry, rz, m, eps2);
         if (use_quad) {
-            const float *q = T.quad + 6 * c;
-            const float tr = q[0] + q[3] + q[5];
-            const float txx = 3.f * q[0] - tr, tyy = 3.f * q[3] - tr, tzz = 3.f * q[5] - tr;
-            const float txy = 3.f * q[1], txz = 3.f * q[2], tyz = 3.f * q[4];
+            const float4 t0 = T.rec[4 * c + 2], t1 = T.rec[4 * c + 3];
+            const float txx = t0.x, txy = t0.y, txz = t0.z, tyy = t0.w, tyz = t1.x, tzz = t1.y;
             const float trx = txx * rx + txy * ry + txz * rz;
             const float try_ = txy * rx + tyy * ry + tyz * rz;
             const float trz = txz * rx + tyz * ry + tzz * rz;
@@ -104,6 +104,22 @@ __device__ float3 evaluate(const WalkTree &T, const WarpLists &W, int ncell, int
         }
     }
     return a;
+}
+
+// Per cell, the four float4 the list evaluation reads: centre and mass, the
+// centre's low part, and the traceless tensor T = 3 Q - tr(Q) I.
+__global__ void walk_pack_kernel(const float *__restrict__ mass, const float *__restrict__ com,
+                                 const float *__restrict__ com_lo, const float *__restrict__ quad,
+                                 int64_t n_cells, float4 *__restrict__ rec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        const float *q = quad + 6 * c;
+        const float tr = q[0] + q[3] + q[5];
+        rec[4 * c] = make_float4(com[3 * c], com[3 * c + 1], com[3 * c + 2], mass[c]);
+        rec[4 * c + 1] = make_float4(com_lo[3 * c], com_lo[3 * c + 1], com_lo[3 * c + 2], 0.f);
+        rec[4 * c + 2] = make_float4(3.f * q[0] - tr, 3.f * q[1], 3.f * q[2], 3.f * q[3] - tr);
+        rec[4 * c + 3] = make_float4(3.f * q[4], 3.f * q[5] - tr, 0.f, 0.f);
+    }
 }
 
 __global__ void walk_groups_kernel(const int32_t *__restrict__ parent, const int32_t *__restrict__ child_first,
@@ -184,10 +200,11 @@ __global__ void __launch_bounds__(kWalkThreads)
                     bool accept = false;
                     if (!meets) {
                         const float l = scalbnf(side, -(int)T.level[c]);
+                        const float4 r0 = T.rec[4 * c], r1 = T.rec[4 * c + 1];
+                        const float cx[3] = {r0.x + r1.x, r0.y + r1.y, r0.z + r1.z};
                         float d2 = 0.f;
                         for (int a = 0; a < 3; ++a) {
-                            const float x = T.com[3 * c + a] + T.com_lo[3 * c + a];
-                            const float u = fmaxf(fmaxf(bmin[a] - x, x - bmax[a]), 0.f);
+                            const float u = fmaxf(fmaxf(bmin[a] - cx[a], cx[a] - bmax[a]), 0.f);
                             d2 = fmaf(u, u, d2);
                         }
                         accept = l * l < theta * theta * d2;
@@ -233,13 +250,14 @@ __global__ void __launch_bounds__(kWalkThreads)
 }  // namespace
 
 int64_t walk_buffer_words(int64_t n_cells) {
-    return 8 + n_cells + (int64_t)kWalkBlocks * kWalkWarps * kStackCap;
+    return 16 * n_cells + 8 + n_cells + (int64_t)kWalkBlocks * kWalkWarps * kStackCap;
 }
 
 cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps, int n_group,
                         int use_quad, float *acc, int32_t *buf, cudaStream_t s) {
-    uint32_t *ctr = reinterpret_cast<uint32_t *>(buf);
-    int32_t *groups = buf + 8;
+    float4 *rec = reinterpret_cast<float4 *>(buf);   // first: 16-byte aligned
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(buf + 16 * t.n_cells);
+    int32_t *groups = buf + 16 * t.n_cells + 8;
     int32_t *stacks = groups + t.n_cells;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
@@ -250,8 +268,11 @@ cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps,
                                                       t.n_cells, n_group, groups, ctr);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    walk_pack_kernel<<<(unsigned)grid, 256, 0, s>>>(t.mass, t.com, t.com_lo, t.quad, t.n_cells, rec);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     WalkTree T{t.child_first, t.child_end, t.pfirst, t.pend, t.level, t.mass, t.com, t.com_lo,
-               t.quad, t.aabb, ws.xs, t.perm, t.side};
+               t.quad, t.aabb, ws.xs, t.perm, t.side, rec};
     walk_kernel<<<kWalkBlocks, kWalkThreads, 0, s>>>(T, groups, ctr, stacks, theta, eps * eps,
                                                      use_quad, acc, ws.info);
     ++g_launches;
