@@ -164,19 +164,16 @@ __global__ void __launch_bounds__(kLcThreads, 3)
                 ml[k0 + j] = (uint16_t)(((mw >> (8 * j)) & 0xffu) | (((Lw >> (8 * j)) & 0xffu) << 8));
         }
     }
-    // histograms of m and L + 1 over the leaf starts (m <= L), one atomic per
-    // distinct value and warp
+    // histograms of m and L + 1 over the leaf starts (m <= L): about one
+    // particle in seven is a start, so plain shared atomics rarely collide
     const int sub = (int)(kLcPer * threadIdx.x / kLvTile);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int m = (mw >> (8 * j)) & 0xff, L = (Lw >> (8 * j)) & 0xff;
-        const bool start = m <= L;
-        const int km = start ? m : 31, kl = start ? L + 1 : 31;
-        const unsigned pm = __match_any_sync(0xffffffffu, km);
-        const unsigned pl = __match_any_sync(0xffffffffu, kl);
-        const int lane = threadIdx.x & 31;
-        if (start && lane == __ffs(pm) - 1) atomicAdd(&hist_m[sub][km], (uint32_t)__popc(pm));
-        if (start && lane == __ffs(pl) - 1) atomicAdd(&hist_l[sub][kl], (uint32_t)__popc(pl));
+        if (m <= L) {
+            atomicAdd(&hist_m[sub][m], 1u);
+            atomicAdd(&hist_l[sub][L + 1], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x < kLcSub * kLevelFields) {
