@@ -101,9 +101,10 @@ def kernel_digest():
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms), kept when they fall inside the timed
+    region (host wall clock), else all of them with a note."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -118,12 +119,20 @@ class Clocks:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def wait_first(self, timeout=5.0):
+        """Block until the sampler has written its first line."""
+        t_end = time.time() + timeout
+        while self.proc and time.time() < t_end:
+            if self.path and os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
+
+    def stop(self, window=None):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -132,26 +141,36 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        inside = rows
+        note = None
+        if window is not None:
+            inside = [r for r in rows if window[0] - 0.06 <= r[0] <= window[1] + 0.06]
+            if not inside:
+                inside, note = rows, "no sample inside the timed region; all samples of the run"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[1] for r in inside]
+        reasons = set().union(*[r[3] for r in inside])
         load = [v for v in sm if v > 0.5 * max(sm)] or sm
-        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(r[2] for r in inside)),
+               "reasons": sorted(reasons), "samples": len(inside)}
+        if note:
+            out["note"] = note
+        return out
 
 
 def gen(wl: str, n_override: int):
@@ -275,9 +294,11 @@ def run_ours(a):
     tree.profile(True)
     tree.stage_times()   # drop anything recorded so far
     clocks = Clocks(local)
+    clocks.start()
+    clocks.wait_first()
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    w_begin = time.time()
     l0 = tb.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -289,8 +310,9 @@ def run_ours(a):
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
+    w_end = time.time()
     barrier()
-    ck = clocks.stop()
+    ck = clocks.stop((w_begin, w_end))
     launches = tb.kernel_launches() - l0
     ms = e0.elapsed_time(e1)
     stages = tree.stage_times()

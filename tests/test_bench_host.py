@@ -70,3 +70,35 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     a = bench.args_()
     assert bench.run_reference(a) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_clock_samples_are_kept_inside_the_timed_region(tmp_path):
+    """The nvidia-smi sampler's rows are filtered to the timed window by their
+    timestamps, throttle reasons are collected, and the median SM clock kept."""
+    import datetime
+    import time as _time
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    now = _time.time()
+
+    def row(dt, sm, reason=""):
+        ts = datetime.datetime.fromtimestamp(now + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        flags = ["Active" if r == reason else "Not Active"
+                 for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")]
+        return ", ".join([ts, "0", str(sm), "2070", "900.0", "0x0"] + flags) + "\n"
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(row(-1.0, 1000, "hw_slowdown") + row(0.05, 2070) + row(0.10, 2050, "sw_power_cap")
+                    + row(2.0, 500))
+    c = bench.Clocks(0)
+    c.proc, c.path, c.f = _Done(), str(path), open(tmp_path / "unused", "w")
+    out = c.stop((now, now + 0.15))
+    assert out["samples"] == 2
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["sm_mhz"] == 2060.0 and out["sm_max_mhz"] == 2070.0
