@@ -74,6 +74,8 @@ def args_():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reorder", action="store_true", help="skip the key-ordered-input build")
     ap.add_argument("--no-walk", action="store_true", help="skip the tree-walk timing")
+    ap.add_argument("--precision-workload", default="stress_2p26", choices=sorted(WORKLOADS),
+                    help="workload of the --precision report")
     ap.add_argument("--keys", default="morton", choices=["morton", "hilbert"],
                     help="particle key order of the timed builds")
     ap.add_argument("--batched-steps", type=int, default=100)
@@ -661,7 +663,7 @@ def run_precision(a):
     import torch
     import oracle
     import paper_2312_06102_gb300 as tb
-    wl = a.workload if a.workload != "clustered_2p27" else "stress_2p26"
+    wl = a.precision_workload
     pos, mass, spec, n = gen(wl, a.n)
     n_crit = a.n_crit or spec["n_crit"]
     idx = oracle.PrefixIndex(pos)
