@@ -386,15 +386,17 @@ def run_ours(a):
         cstream = torch.cuda.Stream()
         tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         torch.cuda.synchronize()
-        # the copy alone, for the record
+        # the copy alone, for the record: the first copy into the fresh buffer
+        # also maps its pages, so the second one is the one timed
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(cstream)
-        with torch.cuda.stream(cstream):
-            p2.copy_(hpos, non_blocking=True)
-            w2.copy_(hmass, non_blocking=True)
-        c1.record(cstream)
-        torch.cuda.synchronize()
+        for rep in range(2):
+            c0.record(cstream)
+            with torch.cuda.stream(cstream):
+                p2.copy_(hpos, non_blocking=True)
+                w2.copy_(hmass, non_blocking=True)
+            c1.record(cstream)
+            torch.cuda.synchronize()
         h2d_ms = c0.elapsed_time(c1)
         barrier()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
