@@ -49,6 +49,25 @@ def test_radix_widths(radix_bits):
     _check(pos, mass, 8, radix_bits=radix_bits)
 
 
+def test_every_sort_variant():
+    """Every compiled radix-sort shape (digit bits, threads, keys per thread)
+    gives the same keys, permutation and cells: the autotuner may pick any.
+    The size spans many tiles of the smallest shape and ends in a ragged
+    tile of every shape; the clusters leave long runs of equal upper bits."""
+    pos, mass = clustered_halos(70_001, 9, n_halo=150)
+    o = oracle.build_tree(pos, 16)
+    m = tb()
+    p = torch.from_numpy(pos).cuda()
+    w = torch.from_numpy(mass).cuda()
+    variants = m.sort_variants()
+    assert len(variants) >= 11
+    for cfg in variants:
+        t = m.build(p, w, n_crit=16, sort_cfg=cfg)
+        torch.cuda.synchronize()
+        assert t.sync() == 0, cfg
+        assert_structure_equal(t, o)
+
+
 @pytest.mark.parametrize("n_crit", [1, 2, 8, 32, 100, 1024])
 def test_n_crit_values(n_crit):
     pos, mass = clustered_halos(60_000, 8, n_halo=200)
