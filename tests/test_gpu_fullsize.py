@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import WORKLOADS, batched_plummer, workload
+from synth import WORKLOADS, batched_plummer, jitter_offsets, workload
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -192,12 +192,34 @@ def test_precision_stress_2p26(mode):
 
 
 def test_batched_4096_sampled_sets():
-    """The full batched workload; the largest set and 30 others checked whole."""
+    """The full batched workload at replay steps 0, 1 and 99: the build is
+    captured in a CUDA graph with a fixed cell capacity (as timed) and replayed
+    on the jittered positions of each step.  At step 0 the largest, the
+    smallest and 30 other sets are checked whole, at steps 1 and 99 the
+    largest and 10 others."""
     from test_gpu_batched import _check_sets, _run
+    m = tb()
     b = batched_plummer(n_sets=4096, seed=4)
-    t, *_ = _run(b.pos, b.mass, b.offsets)
+    t, p, w, off = _run(b.pos, b.mass, b.offsets)
     sizes = np.diff(b.offsets)
     rng = np.random.default_rng(44)
     sets = sorted(set([int(np.argmax(sizes)), int(np.argmin(sizes))] +
                       list(rng.choice(4096, 30, replace=False))))
     _check_sets(t, b.pos, b.mass, b.offsets, 16, sets=sets)
+
+    cap = int(t.n_cells * 1.05) + 4096
+    m.build_batched(p, w, off, cell_capacity=cap, tree=t)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            m.build_batched(p, w, off, cell_capacity=cap, tree=t, stream=s)
+    for step in (1, 99):
+        pj = (b.pos + jitter_offsets(4, step, b.offsets, b.scale)).astype(np.float32)
+        p.copy_(torch.from_numpy(pj))
+        g.replay()
+        torch.cuda.synchronize()
+        assert t.sync() == 0
+        few = sorted(set([int(np.argmax(sizes))] + list(rng.choice(4096, 10, replace=False))))
+        _check_sets(t, pj, b.mass, b.offsets, 16, sets=few)
