@@ -27,7 +27,7 @@ namespace tb {
 namespace {
 
 constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr int kLookWindow = 8;
+constexpr int kLookWindow = 4;
 constexpr uint64_t kFlagIncl = 2ull << 62;
 
 template <int RADIX_BITS, int THREADS, int ITEMS>
