@@ -34,7 +34,7 @@ struct DevInfo {
     float s_hi, s_lo;      // scale ~ s_hi + s_lo
     uint32_t exact_only;   // 1: quantise with FP64 only (extreme ranges)
     uint32_t status;       // kErr* bits
-    uint32_t epoch;        // look-back epoch base of this build
+    uint32_t epoch;        // look-back epoch base of the current tree build
     uint32_t n_leaves;
     int32_t max_depth;
     int32_t pad;
