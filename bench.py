@@ -281,10 +281,13 @@ def run_ours(a):
         log(f"[bench] autotune: {cfg} " + " ".join(f"{k}:{v:.3f}" for k, v in tune_ms.items()))
     # first build sizes the cell arrays; later builds use that capacity and
     # need no host synchronisation
+    torch.cuda.synchronize()
+    t_first = time.perf_counter()
     tree = tb.build(p, w, n_crit=n_crit, sort_cfg=cfg, key_order=ko)
     C = tree.n_cells
     tb.moments(tree, p, w)
     torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - t_first) * 1e3
     for _ in range(a.warmup):
         tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         tb.moments(tree, p, w)
@@ -381,7 +384,10 @@ def run_ours(a):
                               "sort_adjusted_frac": round(sort_adj / build_s / 1e9 / peak, 4)},
            "stage_ms": stage_ms,
            "gpu_launches": int(launches),
-           "clocks": ck}
+           "clocks": ck,
+           "first_call": {"ms": round(first_ms, 3),
+                          "what": "first tb_build + tb_moments on a new tree, wall clock: "
+                                  "allocation, the one cell-count read and the build"}}
 
     # end to end through the C ABI from pinned host buffers: every step copies
     # its positions and masses in and reads its root moments back; the copy of
