@@ -21,8 +21,18 @@
  *    tb_free releases it.  A tree may be passed back to tb_build /
  *    tb_build_batched to be rebuilt in place (its buffers grow when needed).
  *  - Work is enqueued on the caller's stream and runs asynchronously.  The
- *    only host synchronisation is the cell-count read-back of a build whose
- *    params.cell_capacity is 0.
+ *    host waits only in these places: the cell-count read-back of a build
+ *    whose params.cell_capacity is 0; a build or walk that must grow a tree's
+ *    buffers (the device is synchronised before the old ones are freed);
+ *    tb_free; and the calls that return device results to the host
+ *    (tb_tree_status, tb_stage_times, tb_selftest_wait,
+ *    tb_keys_sorted_noalloc).  A rebuild with a fixed capacity into buffers
+ *    that are large enough never waits, and can be captured in a CUDA graph.
+ *  - Threads: the library keeps process-wide state (kernel attributes set
+ *    on first use, the launch counter, the scratch of
+ *    tb_keys_sorted_noalloc).  Calls from several host threads must be
+ *    serialised by the caller; one thread may drive many trees on many
+ *    streams.
  *  - Argument errors are returned at once.  Errors the GPU detects
  *    (non-finite coordinate, cell capacity exceeded, a look-back wait that
  *    ran out) are written to a device status word; the next call that

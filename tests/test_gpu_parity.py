@@ -185,6 +185,43 @@ def test_fixed_capacity_and_rebuild_in_place():
     assert_structure_equal(t, o2)
 
 
+def test_graph_captured_build_and_moments():
+    """A rebuild with a fixed cell capacity into buffers that are large
+    enough never waits on the host, so tb_build + tb_moments can be captured
+    in a CUDA graph once and replayed on new positions of the same count:
+    each replay matches the oracle in structure and moments."""
+    m = tb()
+    n = 50_000
+    sets = [plummer(n, 31), uniform_cube(n, 32), clustered_halos(n, 33, n_halo=60)]
+    trees = [oracle.build_tree(pos, 16) for pos, _ in sets]
+    cap = max(o.n_cells for o in trees) + 64
+    pos0, mass0 = sets[0]
+    p = torch.from_numpy(pos0).cuda()
+    w = torch.from_numpy(mass0).cuda()
+    t = m.build(p, w, n_crit=16, cell_capacity=cap)
+    m.moments(t, p, w)
+    torch.cuda.synchronize()
+    assert t.sync() == 0
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            m.build(p, w, n_crit=16, cell_capacity=cap, tree=t, stream=s)
+            m.moments(t, p, w, stream=s)
+    for (pos, mass), o in zip(sets[1:] + sets[:1], trees[1:] + trees[:1]):
+        p.copy_(torch.from_numpy(pos))
+        w.copy_(torch.from_numpy(mass))
+        g.replay()
+        torch.cuda.synchronize()
+        assert t.sync() == 0
+        assert_structure_equal(t, o)
+        M, com, quad, aabb = oracle.moments(o, pos, mass)
+        em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+        assert bb_ok
+        assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
+
+
 def test_capacity_overflow_reported():
     m = tb()
     pos, mass = uniform_cube(40_000, 9)
