@@ -296,6 +296,32 @@ def test_moments_with_other_arrays_than_the_build():
     assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
 
 
+def test_inputs_not_16_byte_aligned():
+    """Positions and masses that start 4 bytes into their buffers (aligned to
+    4 bytes only) take the scalar load path of the root and key kernels; the
+    tree and moments are the same."""
+    m = tb()
+    pos, mass = clustered_halos(30_001, 17, n_halo=80)
+    n = pos.shape[0]
+    o = oracle.build_tree(pos, 16)
+    pbuf = torch.zeros(3 * n + 1, dtype=torch.float32, device="cuda")
+    wbuf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    p = pbuf[1:].view(n, 3)
+    w = wbuf[1:]
+    p.copy_(torch.from_numpy(pos))
+    w.copy_(torch.from_numpy(mass))
+    assert p.data_ptr() % 16 == 4 and w.data_ptr() % 16 == 4
+    t = m.build(p, w, n_crit=16)
+    m.moments(t, p, w)
+    torch.cuda.synchronize()
+    assert t.sync() == 0
+    assert_structure_equal(t, o)
+    M, com, quad, aabb = oracle.moments(o, pos, mass)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+    assert bb_ok
+    assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
+
+
 def test_deterministic_repeat():
     pos, mass = clustered_halos(1 << 17, 14, n_halo=300)
     t1, p, w = gpu_tree(pos, mass, 16)
