@@ -91,11 +91,13 @@ typedef struct {
                                 >0: fixed capacity, no host sync (graph-capturable) */
     int32_t reorder;         /* 1: tb_moments also writes pos_sorted (particles in key
                                 order, Sec. 2.3 step 3) */
-    int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width) */
-    int32_t sort_threads;    /* 0 = tuned default; else threads per sort tile */
+    int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width);
+                                tb_build only */
+    int32_t sort_threads;    /* 0 = tuned default; else threads per sort tile; tb_build only */
     int32_t sort_items;      /* 0 = tuned default; else keys per thread of a sort tile
-                                (compiled variants: see tb_sort_variant) */
-    int32_t batch_threads;   /* batched build: threads per set, 0 = tuned default */
+                                (compiled variants: see tb_sort_variant); tb_build only */
+    int32_t batch_threads;   /* reserved: the batched build runs one 1024-thread block
+                                per set, whatever the value */
     int32_t key_order;       /* tb_key_order: TB_KEYS_MORTON (default) or TB_KEYS_HILBERT
                                 (tb_build only; tb_build_batched takes Morton keys) */
 } tb_params;
@@ -184,7 +186,11 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
  * Every set must hold at most 2^31 - 1 particles.  With
  * params.cell_capacity > 0 and a tree from an earlier call with the same S
  * and n_total, nothing is allocated and nothing synchronises, so the call can
- * be captured into a CUDA graph and replayed. */
+ * be captured into a CUDA graph and replayed.
+ * Of params it reads n_crit, mom_mode and cell_capacity; key_order must be
+ * TB_KEYS_MORTON.  Its shape is fixed (one 1024-thread block per set, five
+ * 8-bit sort passes over the upper 40 key bits), so radix_bits,
+ * sort_threads, sort_items, batch_threads and reorder are not used. */
 tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_t *d_set_offsets,
                            int32_t n_sets, int64_t n_total, const tb_params *params,
                            tb_stream stream, tb_tree **tree);
