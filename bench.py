@@ -218,7 +218,9 @@ def run_reference(a):
     n_crit = a.n_crit or spec["n_crit"]
     import oracle
     oracle.build()
-    m = min(a.cpu_sample, n)
+    # the per-step sample shrinks as the step count grows, so that the whole
+    # run stays near ten full samples of oracle work (a few minutes)
+    m = min(a.cpu_sample, n, max(1 << 20, (10 * a.cpu_sample) // max(1, a.steps)))
     for _ in range(max(0, min(a.warmup, 1))):
         oracle_rate(pos, mass, n_crit, min(m, 1 << 16))
     times = []
