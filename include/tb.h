@@ -88,7 +88,9 @@ typedef struct {
     int32_t n_crit;          /* a cell with more particles than this is split (Sec. 2.1) */
     int32_t mom_mode;        /* tb_mom_mode */
     int64_t cell_capacity;   /* 0: size the cell arrays exactly (one stream sync);
-                                >0: fixed capacity, no host sync (graph-capturable) */
+                                >0: fixed capacity, no host sync (graph-capturable);
+                                at most 2^31 - 1 (cell indices are int32: a tree
+                                with more cells gives TB_EOVERFLOW) */
     int32_t reorder;         /* 1: tb_moments also writes pos_sorted (particles in key
                                 order, Sec. 2.3 step 3) */
     int32_t radix_bits;      /* 0 = tuned default; else 8..11 (sort digit width);
@@ -174,7 +176,8 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
  * while it made the keys; when d_pos and d_mass are the same pointers the
  * build was given, that snapshot is used, so their contents must not change
  * in between.  Other pointers are read afresh.  Cells of more than 2^20
- * particles are summed in FP64 in every mode. */
+ * particles are summed in FP64 in every mode.  Returns TB_EINVAL when the
+ * tree's last tb_build returned an error before it enqueued every stage. */
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
 
 /* Build S independent trees in one call, moments included.  Particles of set
@@ -234,7 +237,8 @@ tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_
  *                 [n][3] FP32 positions, 4 for masses)
  * The tree must come from tb_build (not tb_build_batched); its perm is read
  * on `stream`, so the build must be ordered before this call.  Returns TB_OK
- * or TB_EINVAL (bad pointer, size or alignment) / TB_ECUDA. */
+ * or TB_EINVAL (bad pointer, size or alignment, a batched tree, or a tree
+ * whose last tb_build did not complete) / TB_ECUDA. */
 tb_status tb_reorder(const tb_tree *tree, const void *d_src, void *d_dst, int64_t row_bytes,
                      tb_stream stream);
 

@@ -182,6 +182,9 @@ class Tree:
     n = property(lambda s: int(s.c.n_particles))
     n_cells = property(lambda s: int(s.c.n_cells))
     n_leaves = property(lambda s: int(s.c.n_leaves))
+    # the cell views never reach past the allocated arrays, also after a
+    # build that ran out of capacity (n_cells then holds the count needed)
+    _nc = property(lambda s: min(int(s.c.n_cells), int(s.c.cell_capacity)))
     max_depth = property(lambda s: int(s.c.max_depth))
     level_offset = property(lambda s: [int(v) for v in s.c.level_offset])
     lo = property(lambda s: [float(v) for v in s.c.lo])
@@ -193,22 +196,22 @@ class Tree:
     perm = property(lambda s: _view(s.c.perm, (s.n,), "i32"))
     pos_sorted = property(lambda s: _view(s.c.pos_sorted, (s.n, 4), "f32"))
     # cell arrays
-    ckey = property(lambda s: _view(s.c.ckey, (s.n_cells,), "u64"))
-    level = property(lambda s: _view(s.c.level, (s.n_cells,), "u8"))
-    parent = property(lambda s: _view(s.c.parent, (s.n_cells,), "i32"))
-    child_first = property(lambda s: _view(s.c.child_first, (s.n_cells,), "i32"))
-    child_end = property(lambda s: _view(s.c.child_end, (s.n_cells,), "i32"))
-    pfirst = property(lambda s: _view(s.c.pfirst, (s.n_cells,), "i32"))
-    pend = property(lambda s: _view(s.c.pend, (s.n_cells,), "i32"))
+    ckey = property(lambda s: _view(s.c.ckey, (s._nc,), "u64"))
+    level = property(lambda s: _view(s.c.level, (s._nc,), "u8"))
+    parent = property(lambda s: _view(s.c.parent, (s._nc,), "i32"))
+    child_first = property(lambda s: _view(s.c.child_first, (s._nc,), "i32"))
+    child_end = property(lambda s: _view(s.c.child_end, (s._nc,), "i32"))
+    pfirst = property(lambda s: _view(s.c.pfirst, (s._nc,), "i32"))
+    pend = property(lambda s: _view(s.c.pend, (s._nc,), "i32"))
     leaf_cell = property(lambda s: _view(s.c.leaf_cell, (s.n_leaves,), "i32"))
-    mass = property(lambda s: _view(s.c.mass, (s.n_cells,), "f32"))
-    com = property(lambda s: _view(s.c.com, (s.n_cells, 3), "f32"))
-    com_lo = property(lambda s: _view(s.c.com_lo, (s.n_cells, 3), "f32"))
-    quad = property(lambda s: _view(s.c.quad, (s.n_cells, 6), "f32"))
-    aabb = property(lambda s: _view(s.c.aabb, (s.n_cells, 6), "f32"))
-    mass64 = property(lambda s: _view(s.c.mass64, (s.n_cells,), "f64"))
-    com64 = property(lambda s: _view(s.c.com64, (s.n_cells, 3), "f64"))
-    quad64 = property(lambda s: _view(s.c.quad64, (s.n_cells, 6), "f64"))
+    mass = property(lambda s: _view(s.c.mass, (s._nc,), "f32"))
+    com = property(lambda s: _view(s.c.com, (s._nc, 3), "f32"))
+    com_lo = property(lambda s: _view(s.c.com_lo, (s._nc, 3), "f32"))
+    quad = property(lambda s: _view(s.c.quad, (s._nc, 6), "f32"))
+    aabb = property(lambda s: _view(s.c.aabb, (s._nc, 6), "f32"))
+    mass64 = property(lambda s: _view(s.c.mass64, (s._nc,), "f64"))
+    com64 = property(lambda s: _view(s.c.com64, (s._nc, 3), "f64"))
+    quad64 = property(lambda s: _view(s.c.quad64, (s._nc, 6), "f64"))
     set_cell_offset = property(lambda s: _view(s.c.set_cell_offset, (s.n_sets + 1,), "i64"))
     set_particle_offset = property(lambda s: _view(s.c.set_particle_offset, (s.n_sets + 1,), "i64"))
     set_root = property(lambda s: _view(s.c.set_root, (s.n_sets, 4), "f64"))

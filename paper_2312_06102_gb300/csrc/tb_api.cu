@@ -170,6 +170,19 @@ void refresh_host(TreeState &S) {
     t.side = h.side;
 }
 
+// Cell indices (parent, children, leaf_cell) are int32: a tree with more
+// cells is refused before anything is allocated or written.  The overflow bit
+// also goes into the device status, so later calls on the tree do nothing
+// and report it.
+tb_status refuse_cell_count(TreeState &S, cudaStream_t s) {
+    if (S.ws.h_info->n_cells <= kMaxCells) return TB_OK;
+    S.ws.h_info->status |= kErrOverflow;
+    cudaError_t e = cudaMemcpyAsync(&S.ws.info->status, &S.ws.h_info->status, sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? TB_EOVERFLOW : from_cuda(e);
+}
+
 tb_status read_info(TreeState &S, cudaStream_t s) {
     cudaError_t e = cudaMemcpyAsync(S.ws.h_info, S.ws.info, sizeof(DevInfo),
                                     cudaMemcpyDeviceToHost, s);
@@ -189,7 +202,7 @@ SortCfg pick_cfg(const tb_params *p) {
 
 bool valid_params(const tb_params *p) {
     return p && p->n_crit >= 1 && p->n_crit <= kMaxNcrit && p->mom_mode >= 0 && p->mom_mode <= 2 &&
-           p->cell_capacity >= 0 &&
+           p->cell_capacity >= 0 && p->cell_capacity <= kMaxCells &&
            (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11)) &&
            (p->key_order == TB_KEYS_MORTON || p->key_order == TB_KEYS_HILBERT) &&
            sort_cfg_valid(pick_cfg(p));
@@ -272,6 +285,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     S->radix_bits = cfg.radix_bits;
     ws.last_stream = s;
     ws.moments_ready = false;
+    ws.cells_ready = false;
     t.n_particles = n;
     t.n_crit = params->n_crit;
     ws.cell_cap_request = params->cell_capacity;
@@ -282,6 +296,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
         for (int a = 0; a < 3; ++a) t.lo[a] = 0.0;
         t.side = 1.0;
         cudaError_t e = cudaMemsetAsync(ws.info, 0, offsetof(DevInfo, sort_tile_ctr), s);
+        ws.cells_ready = e == cudaSuccess;
         return from_cuda(e);
     }
     st = ensure_particles(*S, n, cfg, params->reorder != 0);
@@ -316,12 +331,15 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     if (params->cell_capacity == 0) {
         st = read_info(*S, s);
         if (st != TB_OK) return st;
+        st = refuse_cell_count(*S, s);
+        if (st != TB_OK) return st;
         st = ensure_cells(*S, ws.h_info->n_cells, params->mom_mode == TB_MOM_FP64);
         if (st != TB_OK) return st;
     }
     e = launch_emit(t.pkey, n, params->n_crit, ws, t, s);
     if (e != cudaSuccess) return from_cuda(e);
     mark(ws, "emit", s);
+    ws.cells_ready = true;
     return TB_OK;
 }
 
@@ -352,6 +370,7 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
     if (tree->n_sets != 0) return TB_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (tree->n_particles == 0) return TB_OK;
+    if (!S->ws.cells_ready) return TB_EINVAL;   // the last build did not complete
     const bool fp64 = S->params.mom_mode == TB_MOM_FP64;
     if (fp64 && !tree->mass64) {
         tb_status st = ensure_cells(*S, S->ws.cell_cap, true);
@@ -445,6 +464,8 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
     if (params->cell_capacity == 0) {
         st = read_info(*S, s);
         if (ws.h_info->status & kErrInvalid) return TB_EINVAL;
+        if (st != TB_OK) return st;
+        st = refuse_cell_count(*S, s);
         if (st != TB_OK) return st;
         st = ensure_cells(*S, ws.h_info->n_cells > 0 ? ws.h_info->n_cells : 1,
                           params->mom_mode == TB_MOM_FP64);

@@ -15,6 +15,7 @@ constexpr int kLevels = TB_LEVELS;          // depths 0..21
 constexpr int kDepthMax = TB_DEPTH_MAX;
 constexpr int kLevelFields = kLevels + 1;   // 22 level counters + 1 leaf counter
 constexpr int kMaxNcrit = 1024;
+constexpr int64_t kMaxCells = 2147483647;   // cell indices are int32
 constexpr int64_t kBigCell = int64_t(1) << 20;   // cells above this are summed in FP64
 
 // device status bits (tb_dev_info::status)
@@ -110,6 +111,7 @@ struct Workspace {
     int32_t *walk = nullptr;
     int64_t walk_cap = 0;
     bool moments_ready = false;
+    bool cells_ready = false;     // the last tb_build enqueued every stage
 };
 
 // ------------------------------------------------------------ launchers

@@ -66,6 +66,9 @@ extern "C" tb_status tb_reorder(const tb_tree *tree, const void *d_src, void *d_
     if ((a & 3) || (b & 3)) return TB_EINVAL;
     const uintptr_t bytes = (uintptr_t)n * (uintptr_t)row_bytes;
     if (a < b + bytes && b < a + bytes) return TB_EINVAL;   // overlapping arrays
+    // the permutation is complete only after a build that enqueued every stage
+    const Workspace *ws = static_cast<const Workspace *>(tree->internal);
+    if (!ws || !ws->cells_ready) return TB_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (row_bytes % 16 == 0 && ((a | b) & 15) == 0)

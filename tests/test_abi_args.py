@@ -58,7 +58,7 @@ def test_build_rejects_particle_counts(tb, n):
 @pytest.mark.parametrize("field,value", [
     ("n_crit", 0), ("n_crit", -3), ("n_crit", 1025),
     ("mom_mode", -1), ("mom_mode", 3),
-    ("cell_capacity", -1),
+    ("cell_capacity", -1), ("cell_capacity", 1 << 31),   # cell indices are int32
     ("radix_bits", 7), ("radix_bits", 12),
     ("key_order", 2), ("key_order", -1),
     ("sort_threads", 300), ("sort_items", 5),
@@ -128,7 +128,9 @@ def test_reorder_rejects(tb):
     assert L.tb_reorder(C.byref(t), 1 << 20, (1 << 20) + 800, 16, None) == EINVAL
     t.n_sets = 3            # a batched tree
     assert L.tb_reorder(C.byref(t), 1 << 20, 1 << 24, 16, None) == EINVAL
-    t.n_sets, t.n_particles = 0, 0
+    t.n_sets = 0            # valid arguments, but no completed build behind the tree
+    assert L.tb_reorder(C.byref(t), 1 << 20, 1 << 24, 16, None) == EINVAL
+    t.n_particles = 0
     assert L.tb_reorder(C.byref(t), None, None, 16, None) == 0   # empty tree: nothing to do
 
 
