@@ -24,9 +24,10 @@
  *    host waits only in these places: the cell-count read-back of a build
  *    whose params.cell_capacity is 0; a build or walk that must grow a tree's
  *    buffers (the device is synchronised before the old ones are freed);
- *    tb_free; and the calls that return device results to the host
- *    (tb_tree_status, tb_stage_times, tb_selftest_wait,
- *    tb_keys_sorted_noalloc).  A rebuild with a fixed capacity into buffers
+ *    tb_free; tb_walk on a tree last built with a fixed capacity whose cell
+ *    count has not been read back (it reads it first); and the calls that
+ *    return device results to the host (tb_tree_status, tb_stage_times,
+ *    tb_selftest_wait, tb_keys_sorted_noalloc).  A rebuild with a fixed capacity into buffers
  *    that are large enough never waits, and can be captured in a CUDA graph.
  *  - Threads: the library keeps process-wide state (kernel attributes set
  *    on first use, the launch counter, the scratch of

@@ -162,6 +162,7 @@ tb_status ensure_cells(TreeState &S, int64_t cells, bool fp64) {
 void refresh_host(TreeState &S) {
     const DevInfo &h = *S.ws.h_info;
     tb_tree &t = S.pub;
+    S.ws.host_current = true;
     t.n_cells = h.n_cells;
     t.n_leaves = h.n_leaves;
     t.max_depth = h.max_depth;
@@ -286,6 +287,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     ws.last_stream = s;
     ws.moments_ready = false;
     ws.cells_ready = false;
+    ws.host_current = false;
     t.n_particles = n;
     t.n_crit = params->n_crit;
     ws.cell_cap_request = params->cell_capacity;
@@ -296,7 +298,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
         for (int a = 0; a < 3; ++a) t.lo[a] = 0.0;
         t.side = 1.0;
         cudaError_t e = cudaMemsetAsync(ws.info, 0, offsetof(DevInfo, sort_tile_ctr), s);
-        ws.cells_ready = e == cudaSuccess;
+        ws.cells_ready = ws.host_current = e == cudaSuccess;
         return from_cuda(e);
     }
     st = ensure_particles(*S, n, cfg, params->reorder != 0);
@@ -352,6 +354,13 @@ tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_
     if (tree->n_particles == 0) return TB_OK;
     if (!d_acc || (reinterpret_cast<uintptr_t>(d_acc) & 3u)) return TB_EINVAL;
     if (!S->ws.moments_ready) return TB_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the walk sizes its groups, records and buffer by the cell count: after
+    // a fixed-capacity build that count is read back first (one stream wait)
+    if (!S->ws.host_current) {
+        tb_status st = read_info(*S, s);
+        if (st != TB_OK) return st;
+    }
     const int64_t need = walk_buffer_words(tree->n_cells);
     if (S->ws.walk_cap < need) {
         dev_free(S->ws.walk);
@@ -359,7 +368,6 @@ tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_
         if (!dev_alloc(S->ws.walk, need)) return TB_ENOMEM;
         S->ws.walk_cap = need;
     }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return from_cuda(launch_walk(*tree, S->ws, theta, eps, n_group, use_quad, d_acc, S->ws.walk, s));
 }
 

@@ -112,6 +112,7 @@ struct Workspace {
     int64_t walk_cap = 0;
     bool moments_ready = false;
     bool cells_ready = false;     // the last tb_build enqueued every stage
+    bool host_current = false;    // the tree's host scalars match the last build
 };
 
 // ------------------------------------------------------------ launchers
