@@ -58,7 +58,7 @@ def log(*a):
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clustered_2p27", choices=sorted(
@@ -210,6 +210,22 @@ def whole_job_rate(n_per_rank, steps, world, ms, device="cuda"):
     return ms, n_per_rank * steps * world / (ms / 1e3) / 1e6
 
 
+def per_step_ms(stages, steps):
+    """Median, min and max step time from the (name, ms) stage marks of the
+    timed steps, each of which opens with a "start" mark; None when the marks
+    do not split into `steps` steps."""
+    per_step = []
+    for name, v in stages:
+        if name == "start":
+            per_step.append(0.0)
+        if per_step:
+            per_step[-1] += v
+    if len(per_step) != steps or steps == 0:
+        return None
+    return {"median": round(float(np.median(per_step)), 4), "min": round(min(per_step), 4),
+            "max": round(max(per_step), 4), "from": "stage events of each timed step"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -329,6 +345,13 @@ def run_ours(a):
         raise SystemExit(f"timed build failed: {tb.STATUS[st]}")
     ms, value = whole_job_rate(n, a.steps, world, ms)
 
+    # per-step times from the stage marks: the median over the K steps beside
+    # the K-step mean of `ms_per_step`
+    try:
+        step_ms = per_step_ms(stages, a.steps)
+    except Exception:
+        step_ms = None
+
     # per-stage totals over the timed region
     agg = {}
     for name, v in stages:
@@ -368,7 +391,8 @@ def run_ours(a):
 
     out = {"metric": METRIC, "value": round(value, 2),
            "unit": "Mparticles/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-           "ms_per_step": round(ms / a.steps, 4), "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": round(ms / a.steps, 4), "step_ms": step_ms,
+           "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+u64",
            "data": "synthetic (seeded generator, same draw on every rank)",
            "config": {"workload": a.workload, "n_particles": n, "n_crit": n_crit,

@@ -95,3 +95,13 @@ def test_clock_samples_are_kept_inside_the_timed_region(tmp_path):
     assert out["samples"] == 2
     assert out["reasons"] == ["sw_power_cap"]
     assert out["sm_mhz"] == 2060.0 and out["sm_max_mhz"] == 2070.0
+
+
+def test_per_step_times_from_stage_marks():
+    one = [("start", 0.01), ("root", 0.3), ("keys", 1.0), ("sort_pass", 1.2), ("moments", 1.5)]
+    slow = [("start", 0.01), ("root", 0.3), ("keys", 2.0), ("sort_pass", 1.2), ("moments", 1.5)]
+    r = bench.per_step_ms(one + slow + one, 3)
+    assert r["median"] == round(4.01, 4) and r["min"] == round(4.01, 4)
+    assert r["max"] == round(5.01, 4)
+    assert bench.per_step_ms(one + one, 3) is None          # marks do not split into 3 steps
+    assert bench.per_step_ms([("root", 0.3)] + one, 1)["median"] == round(4.01, 4)
