@@ -211,16 +211,22 @@ def whole_job_rate(n_per_rank, steps, world, ms, device="cuda"):
 
 
 def per_step_ms(stages, steps):
-    """Median, min and max step time from the (name, ms) stage marks of the
-    timed steps, each of which opens with a "start" mark; None when the marks
-    do not split into `steps` steps."""
-    per_step = []
-    for name, v in stages:
-        if name == "start":
+    """Median, min and max step time from the (name, ms) stage intervals of
+    the timed steps; None when they do not split into `steps` steps.
+
+    tb_stage_times names each interval after the event that closes it, and
+    every step records a "start" event first.  The first step's "start"
+    closes no interval, so the intervals up to the first one named "start"
+    belong to step 1, and each later "start" interval (the gap between two
+    steps) opens the next step."""
+    if not stages or steps <= 0:
+        return None
+    per_step = [0.0]
+    for i, (name, v) in enumerate(stages):
+        if name == "start" and i > 0:
             per_step.append(0.0)
-        if per_step:
-            per_step[-1] += v
-    if len(per_step) != steps or steps == 0:
+        per_step[-1] += v
+    if len(per_step) != steps:
         return None
     return {"median": round(float(np.median(per_step)), 4), "min": round(min(per_step), 4),
             "max": round(max(per_step), 4), "from": "stage events of each timed step"}
@@ -376,16 +382,16 @@ def run_ours(a):
                 "traffic": None if traffic is None else round(traffic),
                 "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "mean_launch_ms": round(avg_launch_s * 1e3, 4)}
-    # whole-build bytes: positions read twice (root cell, keys), positions and
-    # masses gathered once (moments), sorted keys + permutation written once,
-    # plus the cell records (29 B structure + 76 B moments)
-    cell_bytes = 105
-    strict = 12 * n + 12 * n + 16 * n + 12 * n + cell_bytes * C
-    # sort-adjusted: add what a full-width LSD sort of b-bit digits must move
-    # beyond one sorted write (the unsorted key write, then 24 B a key for
-    # every pass but the last)
-    b_ = cfg[0] if cfg else 8
-    sort_adj = strict + (-(-63 // b_) - 1) * 24 * n + 8 * n
+    # whole-build ideal bytes B* = 40 N + 90 C: positions read for the root
+    # cell (12 B), positions and masses read once more (16 B), sorted keys and
+    # permutation written once (12 B), and a 90-byte cell record (26 B of
+    # structure, 64 B of moments)
+    strict = 40 * n + 90 * C
+    # sort-adjusted: B* plus what this sort moves beyond one sorted write --
+    # the unsorted key write (8 B), the first pass's key read and write
+    # (20 B), 24 B for each further pass, the run step's key read (8 B):
+    # (24 P + 12) N in all, P the global passes, less the 12 N in B*
+    sort_adj = strict + 24 * passes * n
     build_s = ms / a.steps / 1e3
     stage_ms = {k: round(v[0] / a.steps, 4) for k, v in agg.items()}
 
@@ -423,21 +429,15 @@ def run_ours(a):
         p2, w2 = torch.empty_like(p), torch.empty_like(w)
         bufs = [(p, w), (p2, w2)]
         cstream = torch.cuda.Stream()
+        with torch.cuda.stream(cstream):     # touch the second buffer once
+            p2.copy_(hpos, non_blocking=True)
+            w2.copy_(hmass, non_blocking=True)
         tb.build(p, w, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
         torch.cuda.synchronize()
-        # the copy alone, for the record: the first copy into the fresh buffer
-        # also maps its pages, so the second one is the one timed
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        for rep in range(2):
-            c0.record(cstream)
-            with torch.cuda.stream(cstream):
-                p2.copy_(hpos, non_blocking=True)
-                w2.copy_(hmass, non_blocking=True)
-            c1.record(cstream)
-            torch.cuda.synchronize()
-        h2d_ms = c0.elapsed_time(c1)
         barrier()
+        # every in-loop copy is bracketed by its own events on the copy stream
+        cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         used = [torch.cuda.Event(), torch.cuda.Event()]
         f0 = torch.cuda.Event(enable_timing=True)
@@ -445,13 +445,15 @@ def run_ours(a):
         f0.record(stream)
         cstream.wait_event(f0)
 
-        def copy_in(b_):
+        def copy_in(b_, t_):
+            cev[t_][0].record(cstream)
             with torch.cuda.stream(cstream):
                 bufs[b_][0].copy_(hpos, non_blocking=True)
                 bufs[b_][1].copy_(hmass, non_blocking=True)
+            cev[t_][1].record(cstream)
             copied[b_].record(cstream)
 
-        copy_in(0)
+        copy_in(0, 0)
         for t_ in range(a.steps):
             b_ = t_ % 2
             stream.wait_event(copied[b_])
@@ -464,16 +466,22 @@ def run_ours(a):
             if t_ + 1 < a.steps:
                 if t_ >= 1:
                     cstream.wait_event(used[1 - b_])   # step t - 1 is done with that buffer
-                copy_in(1 - b_)
+                copy_in(1 - b_, t_ + 1)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = f0.elapsed_time(f1)
         ems, evalue = whole_job_rate(n, a.steps, world, ems)
+        copy_ms = [c0.elapsed_time(c1) for c0, c1 in cev]
+        h2d_bytes = int(p.numel() * p.element_size() + w.numel() * w.element_size())
         out["e2e"] = {"value": round(evalue, 2),
-                      "unit": "Mparticles/s", "h2d_bytes_per_step": int(16 * n),
-                      "d2h_bytes_per_step": 40,
-                      "h2d_ms_per_step_alone": round(h2d_ms, 3),
-                      "pipelining": "step t+1's H2D copy overlaps step t's build (two input buffers)"}
+                      "unit": "Mparticles/s", "h2d_bytes_per_step": h2d_bytes,
+                      "d2h_bytes_per_step": int(res.numel() * res.element_size()),
+                      "ms_per_step": round(ems / a.steps, 4),
+                      "h2d_ms_median": round(float(np.median(copy_ms)), 3),
+                      "h2d_gbs_median": round(h2d_bytes / (float(np.median(copy_ms)) / 1e3) / 1e9, 1),
+                      "pipelining": "step t+1's H2D copy overlaps step t's build (two input "
+                                    "buffers); copy times from events around each in-loop copy "
+                                    "on the copy stream"}
         del p2, w2
 
     # key-ordered input: what a simulation sees when it reorders its particle

@@ -97,11 +97,24 @@ def test_clock_samples_are_kept_inside_the_timed_region(tmp_path):
     assert out["sm_mhz"] == 2060.0 and out["sm_max_mhz"] == 2070.0
 
 
+def _library_marks(steps):
+    """Stage intervals as tb_stage_times returns them: events are recorded at
+    "start" and at the end of every stage of each step, and each interval is
+    named after the event that closes it, so the first "start" names none."""
+    events = []
+    for i, keys_ms in enumerate(steps):
+        events += [("start", 0.01), ("root", 0.3), ("keys", keys_ms), ("sort_pass", 1.2),
+                   ("sort_pass", 1.2), ("levels", 0.5), ("emit", 0.4), ("moments", 1.5)]
+    return events[1:]
+
+
 def test_per_step_times_from_stage_marks():
-    one = [("start", 0.01), ("root", 0.3), ("keys", 1.0), ("sort_pass", 1.2), ("moments", 1.5)]
-    slow = [("start", 0.01), ("root", 0.3), ("keys", 2.0), ("sort_pass", 1.2), ("moments", 1.5)]
-    r = bench.per_step_ms(one + slow + one, 3)
-    assert r["median"] == round(4.01, 4) and r["min"] == round(4.01, 4)
-    assert r["max"] == round(5.01, 4)
-    assert bench.per_step_ms(one + one, 3) is None          # marks do not split into 3 steps
-    assert bench.per_step_ms([("root", 0.3)] + one, 1)["median"] == round(4.01, 4)
+    # the gap before each later step's "start" belongs to that step
+    r = bench.per_step_ms(_library_marks([1.0, 2.0, 1.0]), 3)
+    first = 0.3 + 1.0 + 2.4 + 0.9 + 1.5             # no "start" interval
+    assert r["min"] == round(first, 4)
+    assert r["median"] == round(0.01 + first, 4)
+    assert r["max"] == round(0.01 + first + 1.0, 4)
+    assert bench.per_step_ms(_library_marks([1.0] * 20), 20)["median"] > 0
+    assert bench.per_step_ms(_library_marks([1.0, 1.0]), 3) is None   # two steps, not three
+    assert bench.per_step_ms([], 1) is None
