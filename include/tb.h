@@ -30,8 +30,8 @@
  *    tb_selftest_wait, tb_keys_sorted_noalloc).  A rebuild with a fixed capacity into buffers
  *    that are large enough never waits, and can be captured in a CUDA graph.
  *  - Threads: the library keeps process-wide state (kernel attributes set
- *    on first use, the launch counter, the scratch of
- *    tb_keys_sorted_noalloc).  Calls from several host threads must be
+ *    on first use on each device, the launch counter, the wait limit, the
+ *    scratch of tb_keys_sorted_noalloc).  Calls from several host threads must be
  *    serialised by the caller; one thread may drive many trees on many
  *    streams.
  *  - Argument errors are returned at once.  Errors the GPU detects
@@ -278,24 +278,40 @@ const char *tb_stage_name(tb_tree *tree, int32_t i);
  * TB_ETIMEOUT when the wait ran out and the context is still usable. */
 tb_status tb_selftest_wait(int64_t spin_limit, tb_stream stream);
 
-/* Allocation-free keys and sort (this entry point has no counterpart in the
- * paper; it exists for callers of this library that cannot allocate device
- * memory at call time -- for example code running while another component's
- * caching allocator holds the device's free memory, or inside a loop that
- * must not pay cudaMalloc's implicit synchronisation).
- * Computes the same root cube, keys and stable (key, index) sort as tb_build
- * (Sec. 2.2, Sec. 2.3 steps 1 and 2):
+/* Test hook for the bounded waits of the radix sort (Sec. 2.3 step 2): each
+ * pass's look-back on earlier tiles gives up after `polls` polls of a
+ * predecessor that has not published yet (the default, 2^26 polls with a
+ * back-off, is about 17 s) and the build then reports TB_ETIMEOUT.  A small
+ * limit makes a multi-tile sort run out on purpose; its keys and cells are
+ * then not valid, but every access stays in bounds and the next build with
+ * the default limit is correct.  polls = 0 restores the default.  The
+ * setting is process-wide and applies to sorts enqueued after the call.
+ * Returns TB_OK, or TB_EINVAL for polls < 0. */
+tb_status tb_set_wait_limit(int64_t polls);
+
+/* Allocation-free keys and sort.  The paper has no counterpart to this entry
+ * point: it serves callers of this library that cannot allocate device
+ * memory when they call -- for example code that runs while another
+ * component's caching allocator holds the device's free memory, or inside a
+ * loop that must not pay cudaMalloc's implicit synchronisation.
+ * Computes the same root cube, keys and stable (key, index) sort as tb_build:
  *   d_pos   [n][3] FP32 positions (device, caller-owned)
  *   n       0 <= n <= TB_NOALLOC_MAX_N, else TB_EINVAL before any GPU work
  *   d_pkey  [n] out: sorted keys (device, caller-owned, 8-byte aligned)
  *   d_perm  [n] out: original index of each sorted key (device, caller-owned)
  *   h_root  [4] out, host, optional: root corner x y z and side
- * Scratch lives in one fixed file-scope device array (about 15 MB per GPU
- * that loads the library, held until exit); nothing is allocated.  The first
- * call on a device looks up that array's address with the device current.
- * Every call shares the array, so calls whose GPU work overlaps race; order
- * them on one stream.  The call synchronises `stream` before it returns
- * TB_OK, TB_EINVAL, TB_ECUDA, TB_ENONFINITE or TB_ETIMEOUT. */
+ * Scratch lives in one fixed file-scope device array of about 15 MB.  CUDA
+ * loads the library's code lazily, so a device reserves that array at the
+ * first call on it (the call looks up the array's address with the device
+ * current), and loads the kernels at the first call that sorts (n >= 2):
+ * those first calls can return TB_ENOMEM or TB_ECUDA when the device's
+ * memory is already taken.  Make one call with n >= 2 at start-up, before
+ * any stream capture; after it the device holds the array and the kernels
+ * until the process exits and calls allocate nothing.  Every call shares
+ * the array, so calls whose GPU work overlaps race; order them on one
+ * stream.  The call synchronises `stream` before it returns TB_OK,
+ * TB_EINVAL, TB_ENOMEM (first calls on a device only), TB_ECUDA,
+ * TB_ENONFINITE or TB_ETIMEOUT. */
 #define TB_NOALLOC_MAX_N 524288
 tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint64_t *d_pkey, int32_t *d_perm,
                                  double *h_root, tb_stream stream);

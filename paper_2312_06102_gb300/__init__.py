@@ -33,6 +33,7 @@ from ._lib import (  # noqa: F401
     library_path,
     moments,
     selftest_wait,
+    set_wait_limit,
     sort_variants,
     status_string,
 )

@@ -94,6 +94,8 @@ def lib():
         L.tb_reorder.restype = C.c_int
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
         L.tb_selftest_wait.restype = C.c_int
+        L.tb_set_wait_limit.argtypes = [C.c_int64]
+        L.tb_set_wait_limit.restype = C.c_int
         _lib = L
     return _lib
 
@@ -336,3 +338,9 @@ def keys_sorted_noalloc(pos: torch.Tensor, pkey_out: torch.Tensor, perm_out: tor
 
 def selftest_wait(spin_limit: int, stream=None) -> int:
     return int(lib().tb_selftest_wait(int(spin_limit), _stream(stream)))
+
+
+def set_wait_limit(polls: int) -> int:
+    """tb_set_wait_limit: polls after which a radix-pass look-back wait gives
+    up (0 restores the default)."""
+    return int(lib().tb_set_wait_limit(int(polls)))

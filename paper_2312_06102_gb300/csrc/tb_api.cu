@@ -541,6 +541,12 @@ const char *tb_stage_name(tb_tree *tree, int32_t i) {
     return ws.ev_name[i + 1];
 }
 
+tb_status tb_set_wait_limit(int64_t polls) {
+    if (polls < 0) return TB_EINVAL;
+    g_wait_limit = polls > 0 ? polls : kDefaultWaitLimit;
+    return TB_OK;
+}
+
 tb_status tb_selftest_wait(int64_t spin_limit, tb_stream stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint32_t *buf = nullptr;

@@ -477,8 +477,8 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                 ws.perm_alt, ws.xm, ws.xs, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
                 t.set_root, ws.set_ctr, ws.info};
     cudaError_t e;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
         const int sm_front = (int)batch_front_smem(kMaxNcrit);
         cudaFuncSetAttribute(batch_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_front);
         cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -487,7 +487,6 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        attr = true;
     }
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);

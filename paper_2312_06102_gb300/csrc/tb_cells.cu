@@ -435,23 +435,21 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int ncrit, Workspace
                           cudaStream_t s) {
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
     const size_t smem = lv_smem_bytes(ncrit);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
         cudaFuncSetAttribute(level_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lv_smem_bytes(kMaxNcrit));
         cudaFuncSetAttribute(level_count_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        attr = true;
     }
     if (ncrit >= kLcMinN && ncrit <= kLcMaxN) {
-        static bool fast_attr = false;
-        if (!fast_attr) {
+        static std::atomic<uint64_t> fast_attr_done{0};
+        if (first_on_device(fast_attr_done)) {
             cudaFuncSetAttribute(level_count_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)lc_smem_bytes(kLcMaxN));
             cudaFuncSetAttribute(level_count_fast_kernel,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
-            fast_attr = true;
         }
         const int64_t blocks = (n + kLcTile - 1) / kLcTile;
         level_count_fast_kernel<<<(unsigned)blocks, kLcThreads, lc_smem_bytes(ncrit), s>>>(

@@ -3,6 +3,7 @@
 // each kernel family.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
@@ -119,6 +120,8 @@ struct Workspace {
 // Each returns cudaSuccess or the launch error.
 
 extern int64_t g_launches;
+constexpr int64_t kDefaultWaitLimit = int64_t(1) << 26;
+extern int64_t g_wait_limit;   // polls of a radix-pass look-back wait
 
 cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len, cudaStream_t s);
 cudaError_t launch_keys(const float *pos, const float *mass, int64_t n, uint64_t *keys,
@@ -157,5 +160,18 @@ cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps,
                         int use_quad, float *acc, int32_t *buf, cudaStream_t s);
 
 void mark(Workspace &ws, const char *name, cudaStream_t s);
+
+// Kernel attributes (dynamic shared memory above 48 KB, carve-out) belong to
+// a device.  A launcher keeps one bit per device in `done` and sets its
+// attributes the first time it runs on each device; two host threads that
+// race here both set the same values, which is harmless.
+inline bool first_on_device(std::atomic<uint64_t> &done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    const uint64_t bit = uint64_t(1) << dev;
+    if (done.load(std::memory_order_acquire) & bit) return false;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
 
 }  // namespace tb

@@ -299,10 +299,9 @@ static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uin
                      (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
     const float m_eq = (float)(1.0 / (double)(n > 0 ? n : 1));
     size_t smem = sizeof(uint32_t) * passes * (1 << B);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
         cudaFuncSetAttribute(keys_kernel<B, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        attr = true;
     }
     int64_t grid = 152 * 4;
     int64_t need = (n + 4 * kKeysThreads - 1) / (4 * kKeysThreads);

@@ -9,16 +9,23 @@
 // footprint after start-up.  For them this file keeps the sort's scratch --
 // the digit histograms, the look-back array, the second key / index buffer,
 // the (x, y, z, m) records the key kernel writes and the queue of long sort
-// runs -- in one file-scope
-// device array of fixed size.  Every GPU that loads the library holds that
-// array (about 15 MB) until the process exits; particle counts above
-// TB_NOALLOC_MAX_N are refused.
+// runs -- in one file-scope device array of fixed size (about 15 MB);
+// particle counts above TB_NOALLOC_MAX_N are refused.
+//
+// The array belongs to this file's CUDA module.  CUDA loads modules lazily
+// by default, so a device reserves the array when the module is first used
+// there: at the first call on that device, whose address lookup loads it.
+// The kernels' modules load the same way at the first call that sorts
+// (n >= 2).  Those first calls can therefore fail when the device's memory
+// is already taken; a caller makes one call with n >= 2 at start-up, and
+// from then on the device holds the array and the kernels until the process
+// exits and no call allocates.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents: each call clears the parts that must start at zero (the build
-// record with its counters, and the look-back array).  Calls whose work
-// overlaps on the GPU race on it, so callers must order them (one stream, or
-// events between streams).
+// record with its counters, and the look-back words of the tiles it sorts).
+// Calls whose work overlaps on the GPU race on it, so callers must order
+// them (one stream, or events between streams).
 #include <cstring>
 #include <mutex>
 
@@ -109,9 +116,16 @@ extern "C" tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint6
     if (long_run_capacity(kNoAllocMaxN) > (int64_t)kRunsCap) return TB_ECUDA;
 
     // what must start at zero: the build record and its counters, and the
-    // look-back words
+    // look-back words of this call's tiles.  The record is cleared, so every
+    // call runs with the same look-back epoch and the words a larger earlier
+    // call left would read as published; a tile only reads the words of
+    // tiles before it, so clearing this call's tiles is enough.
+    const SortCfg cfg = default_sort_cfg(kNoAllocRadixBits);
+    const int64_t look_words = ((n + cfg.tile() - 1) / cfg.tile()) << cfg.radix_bits;
+    if (look_words > (int64_t)kLookWords) return TB_ECUDA;
     if ((e = cudaMemsetAsync(ws.info, 0, sizeof(DevInfo), s)) != cudaSuccess) return status_of(e);
-    if ((e = cudaMemsetAsync(ws.lookback, 0, sizeof(uint64_t) * kLookWords, s)) != cudaSuccess)
+    if (look_words > 0 &&
+        (e = cudaMemsetAsync(ws.lookback, 0, sizeof(uint64_t) * look_words, s)) != cudaSuccess)
         return status_of(e);
     if (n == 0) {
         if (h_root) {
@@ -120,7 +134,6 @@ extern "C" tb_status tb_keys_sorted_noalloc(const float *d_pos, int64_t n, uint6
         }
         return status_of(cudaStreamSynchronize(s));
     }
-    const SortCfg cfg = default_sort_cfg(kNoAllocRadixBits);
     const int passes = sort_plan(cfg).passes;
     if ((e = launch_root(d_pos, n, ws, passes << cfg.radix_bits, s)) != cudaSuccess)
         return status_of(e);

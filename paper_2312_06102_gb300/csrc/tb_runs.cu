@@ -115,11 +115,10 @@ cudaError_t launch_runs(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t 
     const RunBuffers rb = run_buffers(long_runs, n);
     if (shift0 <= 0 || n <= 1) return cudaSuccess;
     if (shift0 > 32) return cudaErrorInvalidValue;   // the run step ranks the low bits as 32-bit words
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
         cudaFuncSetAttribute(long_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(CtaSortShared));
-        attr = true;
     }
     const int64_t tiles = (n + kRunTile - 1) / kRunTile;
     run_sort_kernel<<<(unsigned)tiles, kRunThreads, 0, s>>>(keys, vals, n, shift0, rb, ws.info);

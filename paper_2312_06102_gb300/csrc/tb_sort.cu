@@ -272,8 +272,8 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
                        cudaStream_t s) {
     using S = SortSmem<B, T, I>;
     const size_t smem = sizeof(S);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
         cudaFuncSetAttribute(onesweep_kernel<B, T, I, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(onesweep_kernel<B, T, I, false>,
@@ -284,13 +284,12 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
         cudaFuncSetAttribute(onesweep_kernel<B, T, I, false>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        attr = true;
     }
     const int64_t tiles = (n + S::TILE - 1) / S::TILE;
     // the unsorted keys are in `ka`; passes alternate ka -> kb -> ka ...
     uint64_t *src = ka, *dst = kb;
     int32_t *vsrc = pa, *vdst = pb;
-    const int64_t spin = int64_t(1) << 26;
+    const int64_t spin = g_wait_limit;
     for (int p = 0; p < plan.passes; ++p) {
         if (p == 0)
             onesweep_kernel<B, T, I, true><<<(unsigned)tiles, T, smem, s>>>(
@@ -317,6 +316,10 @@ cudaError_t run_passes(uint64_t *ka, uint64_t *kb, int32_t *pa, int32_t *pb, int
 }
 
 }  // namespace
+
+// Polls after which a look-back wait gives up (about 17 s with the back-off);
+// tb_set_wait_limit lowers it to exercise the timeout path.
+int64_t g_wait_limit = kDefaultWaitLimit;
 
 // Compiled variants: digit bits, threads per tile, keys per thread.
 static const SortCfg kVariants[] = {

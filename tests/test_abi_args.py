@@ -146,3 +146,9 @@ def test_keys_noalloc_rejects(tb):
     assert L.tb_keys_sorted_noalloc(18, 10, 64, 32, root, None) == EINVAL   # positions
     assert L.tb_keys_sorted_noalloc(16, 10, 68, 32, root, None) == EINVAL   # keys need 8 B
     assert L.tb_keys_sorted_noalloc(16, 10, 64, 34, root, None) == EINVAL   # permutation
+
+
+def test_wait_limit_setter(tb):
+    assert tb.lib().tb_set_wait_limit(-1) == EINVAL
+    assert tb.lib().tb_set_wait_limit(5) == 0
+    assert tb.lib().tb_set_wait_limit(0) == 0      # back to the default
