@@ -109,7 +109,9 @@ tb_status ensure_fixed(TreeState &S) {
     return TB_OK;
 }
 
-tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reorder) {
+// need_xs: the key-ordered records are scratch of the batched build's moments
+tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reorder,
+                           bool need_xs) {
     Workspace &ws = S.ws;
     tb_tree &t = S.pub;
     const int64_t tiles = (n + cfg.tile() - 1) / cfg.tile();
@@ -121,7 +123,7 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         int64_t cap = n;
         int64_t lb = need_lb > 0 ? need_lb : 1;
         if (!dev_alloc(t.pkey, cap) || !dev_alloc(t.perm, cap) || !dev_alloc(ws.keys_alt, cap) ||
-            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) || !dev_alloc(ws.xs, cap) ||
+            !dev_alloc(ws.perm_alt, cap) || !dev_alloc(t.leaf_cell, cap) || !dev_alloc(ws.xm, cap) ||
             !dev_alloc(ws.big_leaf, cap) || !dev_alloc(ws.ml, cap) ||
             !dev_alloc(ws.long_runs, long_run_capacity(cap)) ||
             !dev_alloc(ws.level_cnt, (ltiles + 1) * kLevelFields) || !dev_alloc(ws.lookback, lb))
@@ -131,8 +133,9 @@ tb_status ensure_particles(TreeState &S, int64_t n, const SortCfg &cfg, bool reo
         ws.tiles_cap = lb;
         ws.level_tiles_cap = ltiles;
     }
-    // the key-ordered records the moments are summed from are the reorder
-    // output of Sec. 2.3 step 3; they are exposed when asked for
+    // the particles in key order (the reorder output of Sec. 2.3 step 3) are
+    // written out by the leaf pass only when asked for
+    if ((reorder || need_xs) && !ws.xs && !dev_alloc(ws.xs, ws.n_cap)) return TB_ENOMEM;
     t.pos_sorted = reorder ? reinterpret_cast<float *>(ws.xs) : nullptr;
     return TB_OK;
 }
@@ -286,6 +289,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     S->radix_bits = cfg.radix_bits;
     ws.last_stream = s;
     ws.moments_ready = false;
+    ws.xs_current = false;
     ws.cells_ready = false;
     ws.host_current = false;
     t.n_particles = n;
@@ -301,7 +305,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
         ws.cells_ready = ws.host_current = e == cudaSuccess;
         return from_cuda(e);
     }
-    st = ensure_particles(*S, n, cfg, params->reorder != 0);
+    st = ensure_particles(*S, n, cfg, params->reorder != 0, false);
     if (st != TB_OK) return st;
     if (params->cell_capacity > 0) {
         st = ensure_cells(*S, params->cell_capacity, params->mom_mode == TB_MOM_FP64);
@@ -368,6 +372,14 @@ tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_
         if (!dev_alloc(S->ws.walk, need)) return TB_ENOMEM;
         S->ws.walk_cap = need;
     }
+    // the walk reads the particles in key order: written by the moments only
+    // when pos_sorted was asked for, else gathered here once per moments call
+    if (!S->ws.xs_current) {
+        if (!S->ws.xs && !dev_alloc(S->ws.xs, S->ws.n_cap)) return TB_ENOMEM;
+        cudaError_t e = launch_gather_records(tree->perm, S->ws.xm, S->ws.xs, tree->n_particles, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        S->ws.xs_current = true;
+    }
     return from_cuda(launch_walk(*tree, S->ws, theta, eps, n_group, use_quad, d_acc, S->ws.walk, s));
 }
 
@@ -397,6 +409,7 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
     e = launch_moments(*tree, S->ws, S->params.mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
     S->ws.moments_ready = true;
+    S->ws.xs_current = tree->pos_sorted != nullptr;
     return TB_OK;
 }
 
@@ -428,7 +441,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
     t.n_particles = n_total;
     t.n_crit = params->n_crit;
     t.n_sets = n_sets;
-    st = ensure_particles(*S, n_total, default_sort_cfg(8), false);
+    st = ensure_particles(*S, n_total, default_sort_cfg(8), false, true);
     if (st != TB_OK) return st;
     if (n_sets > ws.set_cap || !t.set_cell_offset) {
         cudaDeviceSynchronize();

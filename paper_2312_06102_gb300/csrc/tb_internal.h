@@ -77,7 +77,7 @@ struct Workspace {
     int64_t reorder_cap = 0;
 
     float4 *xm = nullptr;            // [n] (x, y, z, m) in input order, written with the keys
-    float4 *xs = nullptr;            // [n] the same records in key order (moments)
+    float4 *xs = nullptr;            // [n] the same records in key order (reorder only)
     const float *xm_pos = nullptr;   // arrays xm was made from
     const float *xm_mass = nullptr;
     uint64_t *keys_alt = nullptr;
@@ -112,6 +112,7 @@ struct Workspace {
     int32_t *walk = nullptr;
     int64_t walk_cap = 0;
     bool moments_ready = false;
+    bool xs_current = false;      // xs holds the records of the last moments in key order
     bool cells_ready = false;     // the last tb_build enqueued every stage
     bool host_current = false;    // the tree's host scalars match the last build
 };
@@ -136,6 +137,8 @@ cudaError_t launch_levels(const uint64_t *skeys, int64_t n, int n_crit, Workspac
 cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int n_crit, Workspace &ws,
                         tb_tree &t, cudaStream_t s);
 cudaError_t launch_moments(tb_tree &t, Workspace &ws, int mode, cudaStream_t s);
+cudaError_t launch_gather_records(const int32_t *perm, const float4 *xm, float4 *xs, int64_t n,
+                                  cudaStream_t s);
 cudaError_t launch_wait_selftest(int64_t limit, uint32_t *status, uint32_t *flag, cudaStream_t s);
 
 int level_tile_size();

@@ -2,11 +2,13 @@
 // properties are computed as cells are created; the centre of mass of a
 // parent comes from those of its children, higher multipoles likewise).
 //
-//   gather_kernel        : particles in key order, (x, y, z, m) records
-//                          (Sec. 2.3 step 3, the reorder); every thread keeps
-//                          four independent gathers in flight;
-//   leaf_moments_kernel  : every leaf sums its contiguous members (leaves in
-//                          key order, one launch for all levels);
+//   leaf_tile_kernel     : every leaf, one block per tile of 2048 positions in
+//                          key order: the tile's permutation bulk-copied (TMA)
+//                          into shared memory, its (x, y, z, m) records
+//                          gathered beside it (Sec. 2.3 step 3, the reorder),
+//                          one thread per leaf summing from there;
+//   long_leaf_kernel     : leaves the tile could not hold, members read
+//                          through the permutation;
 //   big_leaf_kernel      : depth-21 leaves of identical keys that are too long
 //                          for one thread, summed block-wide;
 //   level_moments_kernel : one launch per level, deepest first: every other
@@ -37,78 +39,264 @@ namespace {
 
 // ------------------------------------------------------------ kernels
 
-// xs[k] = xm[perm[k]]: the particles in key order.
-__global__ void __launch_bounds__(256)
-    gather_kernel(const int32_t *__restrict__ perm, const float4 *__restrict__ xm,
-                  float4 *__restrict__ xs, int64_t n, const DevInfo *info) {
-    if (info->status & kErrNonFinite) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n4 = n / 4;
-    const int4 *p4 = reinterpret_cast<const int4 *>(perm);
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += stride) {
-        const int4 id = __ldcs(p4 + g);
-        const float4 a = __ldg(xm + id.x), b = __ldg(xm + id.y), c = __ldg(xm + id.z),
-                     d = __ldg(xm + id.w);
-        xs[4 * g] = a;
-        xs[4 * g + 1] = b;
-        xs[4 * g + 2] = c;
-        xs[4 * g + 3] = d;
-    }
-    for (int64_t k = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
-        xs[k] = __ldg(xm + perm[k]);
-}
+// Leaves, one block per tile of kLtTile consecutive key-order positions.
+//   1. The permutation of the tile and of a halo of kLtHalo positions past
+//      it is bulk-copied (TMA) into shared memory, and m_k | L_k << 8 of the
+//      same positions is read beside it.
+//   2. The records (x, y, z, m) of those particles are gathered into shared
+//      memory: xm[perm[k]] (Sec. 2.3 step 3).  When the permutation of the
+//      span is one ascending run -- input already in key order, as after a
+//      reorder -- the records are one contiguous stretch and come in with one
+//      bulk copy instead.  With `xs` set (pos_sorted asked for), the tile's
+//      records are bulk-stored to it.
+//   3. k starts a leaf iff m_k <= L_k (Alg. 1 as a closed form); leaves tile
+//      the key order, so a leaf ends where the next one starts.  The leaves
+//      starting in the tile are listed in order; their index among all
+//      leaves comes from the scanned per-tile leaf counts of the cell pass.
+//   4. One thread per leaf sums its members from shared memory.  A leaf that
+//      runs past the staged span (only a depth-21 leaf of identical keys, or
+//      n_crit above the halo, can) and, in the compensated mode, a leaf of
+//      more than kSplitLeaf members go to the queue of long_leaf_kernel.
+constexpr int kLtThreads = 256;
+constexpr int kLtTile = 2048;                  // two cell-pass tiles of 1024
+constexpr int kLtHalo = 64;
+constexpr int kLtSpan = kLtTile + kLtHalo;
+constexpr int kLtPer = kLtTile / kLtThreads;   // positions per thread when listing starts
+static_assert(kLtTile == 2 * 1024, "leaf tiles span two tiles of the cell pass");
 
-// Every leaf, in key order (so a warp reads one stretch of the records).
-// Leaves longer than kBigLeafThread -- only depth-21 leaves of identical keys
-// can be -- are queued for big_leaf_kernel.
+struct LeafTileSmem {
+    float4 rec[kLtSpan];
+    int32_t perm[kLtSpan];
+    uint16_t ml[kLtSpan];
+    uint16_t start[kLtTile];                   // offsets of the leaf starts in the tile
+    uint32_t wcount[kLtThreads / 32];
+    int32_t next_start;                        // first start at or past the tile end, or -1
+    uint64_t bar;
+};
+
+size_t leaf_tile_smem() { return sizeof(LeafTileSmem); }
+
 template <int MODE>
-__global__ void __launch_bounds__(kMomThreads, 3)
-    leaf_moments_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell,
-                        const float4 *__restrict__ xs, DevInfo *info) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    const int64_t nl = info->n_leaves;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
-        const int64_t c = leaf_cell[j];
-        const int64_t pf = T.pfirst[c], pe = T.pend[c];
-        if (pe - pf > kBigLeafThread) {
-            const uint32_t q = atomicAdd(&info->misc_ctr[2], 1u);
-            T.big_leaf[q] = (int32_t)c;
+__global__ void __launch_bounds__(kLtThreads, 4)
+    leaf_tile_kernel(MomOut o, const int32_t *__restrict__ leaf_cell,
+                     const int32_t *__restrict__ perm, const float4 *__restrict__ xm,
+                     const uint16_t *__restrict__ ml, const uint32_t *__restrict__ leaf_off,
+                     int64_t n, float4 *__restrict__ xs, int32_t *long_queue, DevInfo *info,
+                     int64_t wait_limit) {
+    if (info->status & (kErrOverflow | kErrNonFinite | kErrTimeout)) return;
+    extern __shared__ __align__(128) unsigned char lt_raw[];
+    LeafTileSmem &S = *reinterpret_cast<LeafTileSmem *>(lt_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * kLtTile;
+    const int span = (int)min64(kLtSpan, n - k0);
+    const int te = (int)min64(kLtTile, n - k0);
+    // 1. permutation of the span: its whole 16-byte groups by bulk copy
+    //    (k0 is a multiple of 4), the rest by plain loads
+    const int nbulk = span & ~3;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar, 1);
+        mbar_init_fence();
+        if (nbulk > 0) {
+            mbar_arrive_expect_tx(&S.bar, (uint32_t)nbulk * 4u);
+            bulk_load(S.perm, perm + k0, (uint32_t)nbulk * 4u, &S.bar);
+        }
+    }
+    for (int x = nbulk + (int)threadIdx.x; x < span; x += kLtThreads) S.perm[x] = perm[k0 + x];
+    for (int x = threadIdx.x; x < span; x += kLtThreads) S.ml[x] = ml[k0 + x];
+    __syncthreads();
+    uint32_t phase = 0;
+    bool ok = true;
+    if (nbulk > 0) {
+        ok = mbar_wait_bounded(&S.bar, phase, wait_limit);
+        phase ^= 1u;
+    }
+    // a copy that did not complete: record it and leave once it has
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) {
+            flag_error(&info->status, kErrTimeout);
+            mbar_wait_bounded(&S.bar, 0, wait_limit);
+        }
+        return;
+    }
+    // 2. records of the span
+    bool run = true, in_range = true;
+    for (int x = threadIdx.x; x < span; x += kLtThreads) {
+        const int32_t p = S.perm[x];
+        in_range &= (uint32_t)p < (uint32_t)n;
+        if (x + 1 < span) run &= S.perm[x + 1] == p + 1;
+    }
+    if (!__syncthreads_and(in_range)) {
+        if (threadIdx.x == 0) flag_error(&info->status, kErrTimeout);
+        return;
+    }
+    if (__syncthreads_and(run)) {
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&S.bar, (uint32_t)span * 16u);
+            bulk_load(S.rec, xm + S.perm[0], (uint32_t)span * 16u, &S.bar);
+        }
+        ok = mbar_wait_bounded(&S.bar, phase, wait_limit);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                flag_error(&info->status, kErrTimeout);
+                mbar_wait_bounded(&S.bar, phase, wait_limit);
+            }
+            return;
+        }
+    } else {
+        // random gather: every record of the span in flight at once, by
+        // asynchronous copies that hold no registers
+        for (int x = threadIdx.x; x < span; x += kLtThreads) cp_async16(&S.rec[x], xm + S.perm[x]);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    // the reordered records, when asked for, go out by one bulk store (every
+    // thread orders its shared-memory writes before the store reads them)
+    if (xs) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_store(xs + k0, S.rec, (uint32_t)te * 16u);
+    }
+    // 3. leaf starts of the tile, in order
+    uint32_t flags = 0;
+#pragma unroll
+    for (int j = 0; j < kLtPer; ++j) {
+        const int x = threadIdx.x * kLtPer + j;
+        if (x < te) {
+            const uint32_t v = S.ml[x];
+            if ((v & 0xffu) <= (v >> 8)) flags |= 1u << j;
+        }
+    }
+    const uint32_t cnt = __popc(flags);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) S.wcount[warp] = incl;
+    // the first start at or past the tile's end, from the halo: warp 0
+    if (warp == 0) {
+        int32_t nx = -1;
+        for (int x0 = te; x0 < span && nx < 0; x0 += 32) {
+            const int x = x0 + lane;
+            bool st = false;
+            if (x < span) {
+                const uint32_t v = S.ml[x];
+                st = (v & 0xffu) <= (v >> 8);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, st);
+            if (b) nx = x0 + __ffs(b) - 1;
+        }
+        // the end of the array ends the last leaf
+        if (nx < 0 && k0 + span == n) nx = span;
+        if (lane == 0) S.next_start = nx;
+    }
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < kLtThreads / 32; ++w) {
+        const uint32_t c = S.wcount[w];
+        if (w < warp) before += c;
+        total += c;
+    }
+    uint32_t pos = before + incl - cnt;
+#pragma unroll
+    for (int j = 0; j < kLtPer; ++j)
+        if (flags & (1u << j)) S.start[pos++] = (uint16_t)(threadIdx.x * kLtPer + j);
+    __syncthreads();
+    // 4. one thread per leaf
+    const uint32_t jbase = leaf_off[2 * blockIdx.x];
+    const int32_t nxt = S.next_start;
+    for (uint32_t r = threadIdx.x; r < total; r += kLtThreads) {
+        const int x = S.start[r];
+        const int xe = (r + 1 < total) ? (int)S.start[r + 1] : nxt;
+        const int64_t c = leaf_cell[jbase + r];
+        const bool staged = xe >= 0;
+        if (!staged) {
+            long_queue[atomicAdd(&info->misc_ctr[5], 1u)] = (int32_t)c;
             continue;
         }
-        leaf_sum<MODE>(o, xs, c, pf, pe);
+        if (MODE == TB_MOM_FP32_COMP && xe - x > kSplitLeaf) {
+            long_queue[atomicAdd(&info->misc_ctr[5], 1u)] = (int32_t)c;
+            continue;
+        }
+        if constexpr (MODE == TB_MOM_FP32_COMP) leaf_sum_split(o, (const float4 *)S.rec, c, x, xe);
+        else leaf_sum<MODE>(o, (const float4 *)S.rec, c, x, xe);
     }
+    if (xs && threadIdx.x == 0) bulk_store_wait_read();
 }
 
-// Compensated mode: every leaf of at most kSplitLeaf members, in key order,
-// with the split sums only (few registers, many warps in flight); longer
-// leaves are queued for mid_leaf_kernel (compensated sums) or, beyond
-// kBigLeafThread, for big_leaf_kernel.
+// Shuffle every field of an accumulator down the warp by `off` lanes.
+template <class Acc>
+__device__ __forceinline__ Acc shfl_down_acc(const Acc &a, int off) {
+    Acc b;
+    constexpr int W = sizeof(Acc) / 4;
+    static_assert(sizeof(Acc) % 4 == 0, "accumulators are made of 4-byte words");
+    const uint32_t *u = reinterpret_cast<const uint32_t *>(&a);
+    uint32_t *v = reinterpret_cast<uint32_t *>(&b);
+#pragma unroll
+    for (int i = 0; i < W; ++i) v[i] = __shfl_down_sync(0xffffffffu, u[i], off);
+    return b;
+}
+
+// The queued leaves, one warp per leaf, members read through the
+// permutation (32 independent loads per round): each lane sums a stride of
+// the members about the leaf's first member, then the lanes' sums merge in a
+// fixed tree (compensated merges in the compensated mode).  Leaves of more
+// than kBigLeafThread members -- only depth-21 leaves of identical keys --
+// are queued again for big_leaf_kernel.
+template <int MODE>
 __global__ void __launch_bounds__(kMomThreads, 4)
-    leaf_split_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell,
-                      const float4 *__restrict__ xs, int32_t *mid_queue, DevInfo *info) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    const int64_t nl = info->n_leaves;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += stride) {
-        const int64_t c = leaf_cell[j];
-        const int64_t pf = T.pfirst[c], pe = T.pend[c];
-        if (pe - pf > kBigLeafThread) T.big_leaf[atomicAdd(&info->misc_ctr[2], 1u)] = (int32_t)c;
-        else if (pe - pf > kSplitLeaf) mid_queue[atomicAdd(&info->misc_ctr[5], 1u)] = (int32_t)c;
-        else leaf_sum_split(o, xs, c, pf, pe);
-    }
-}
-
-// Compensated mode: the queued leaves of kSplitLeaf + 1 .. kBigLeafThread members.
-__global__ void __launch_bounds__(kMomThreads, 3)
-    mid_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, const int32_t *mid_queue,
-                    DevInfo *info) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    long_leaf_kernel(TreeIn T, MomOut o, PermSrc src, const int32_t *long_queue, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite | kErrTimeout)) return;
+    using Acc = typename std::conditional<
+        MODE == TB_MOM_FP64, AccD,
+        typename std::conditional<MODE == TB_MOM_FP32_COMP, AccC, AccP>::type>::type;
+    const int lane = threadIdx.x & 31;
     const int64_t nq = *(volatile const uint32_t *)&info->misc_ctr[5];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride) {
-        const int64_t c = mid_queue[q];
-        leaf_sum<TB_MOM_FP32_COMP>(o, xs, c, T.pfirst[c], T.pend[c]);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; q < nq; q += nwarps) {
+        const int64_t c = long_queue[q];
+        const int64_t pf = T.pfirst[c], pe = T.pend[c];
+        if (pe - pf > kBigLeafThread) {
+            if (lane == 0) T.big_leaf[atomicAdd(&info->misc_ctr[2], 1u)] = (int32_t)c;
+            continue;
+        }
+        const float4 r0 = src[pf];
+        const float ref[3] = {r0.x, r0.y, r0.z};
+        float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+        Acc A;
+        A.init();
+        for (int64_t k = pf + lane; k < pe; k += 32) {
+            const float4 v = src[k];
+            const float x[3] = {v.x, v.y, v.z};
+            for (int a = 0; a < 3; ++a) {
+                bb[a] = fminf(bb[a], x[a]);
+                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+            }
+            if constexpr (MODE == TB_MOM_FP64) {
+                const double dx[3] = {(double)x[0] - (double)ref[0], (double)x[1] - (double)ref[1],
+                                      (double)x[2] - (double)ref[2]};
+                A.add((double)v.w, dx);
+            } else {
+                const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
+                                     __fsub_rn(x[2], ref[2])};
+                A.add(v.w, dx);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const Acc B = shfl_down_acc(A, off);
+            A.merge(B);
+            for (int a = 0; a < 3; ++a) {
+                bb[a] = fminf(bb[a], __shfl_down_sync(0xffffffffu, bb[a], off));
+                bb[3 + a] = fmaxf(bb[3 + a], __shfl_down_sync(0xffffffffu, bb[3 + a], off));
+            }
+        }
+        if (lane == 0) {
+            if constexpr (MODE == TB_MOM_FP64) finish_d(o, c, A, ref, bb, true);
+            else if constexpr (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
+            else finish_p(o, c, A, ref, bb);
+        }
     }
 }
 
@@ -142,8 +330,8 @@ __global__ void __launch_bounds__(kMomThreads, 4)
 // Block-wide sums of the long depth-21 leaves queued by the leaf launch.
 template <int MODE>
 __global__ void __launch_bounds__(kBigThreads)
-    big_leaf_kernel(TreeIn T, MomOut o, const float4 *__restrict__ xs, DevInfo *info) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
+    big_leaf_kernel(TreeIn T, MomOut o, PermSrc xs, DevInfo *info) {
+    if (info->status & (kErrOverflow | kErrNonFinite | kErrTimeout)) return;
     __shared__ uint32_t s_q;
     __shared__ float s_bb[kBigThreads][6];
     __shared__ double s_d[kBigThreads][10];
@@ -273,41 +461,41 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
     const int64_t n = t.n_particles;
-    // misc_ctr[2..3]: big-leaf queue and tickets; [5]: mid-leaf queue
+    // misc_ctr[2..3]: big-leaf queue and tickets; [5]: long-leaf queue
     cudaError_t e = cudaMemsetAsync(&ws.info->misc_ctr[2], 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    int64_t g = (n / 4 + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
-    if (g < 1) g = 1;
-    gather_kernel<<<(unsigned)g, 256, 0, s>>>(t.perm, ws.xm, ws.xs, n, ws.info);
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
+        cudaFuncSetAttribute(leaf_tile_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)leaf_tile_smem());
+        cudaFuncSetAttribute(leaf_tile_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    }
+    // the long-leaf queue (at most n / 2 leaves of two or more members past
+    // the first) sits in the upper half of the big-leaf buffer (at most
+    // n / 2049 entries in the lower)
+    int32_t *longq = ws.big_leaf + (n + 1) / 2;
+    const int64_t tiles = (n + kLtTile - 1) / kLtTile;
+    const int64_t level_tiles = (n + level_tile_size() - 1) / level_tile_size();
+    const uint32_t *leaf_off = ws.level_cnt + (int64_t)kLevels * level_tiles;
+    leaf_tile_kernel<MODE><<<(unsigned)tiles, kLtThreads, leaf_tile_smem(), s>>>(
+        o, t.leaf_cell, t.perm, ws.xm, ws.ml, leaf_off, n,
+        t.pos_sorted ? reinterpret_cast<float4 *>(t.pos_sorted) : nullptr, longq, ws.info,
+        g_wait_limit);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mark(ws, "gather", s);
+    const PermSrc src{ws.xm, t.perm};
+    long_leaf_kernel<MODE><<<152 * 2, kMomThreads, 0, s>>>(T, o, src, longq, ws.info);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, src, ws.info);
+    ++g_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(ws, "leaves", s);
     // one persistent grid per launch; a level holds at most n cells
     int64_t grid = (n + kMomThreads - 1) / kMomThreads;
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
-    if constexpr (MODE == TB_MOM_FP32_COMP) {
-        // the mid-leaf queue (at most n / 17 leaves) sits in the upper half
-        // of the big-leaf buffer (at most n / 2049 entries in the lower)
-        int32_t *mid = ws.big_leaf + (n + 1) / 2;
-        leaf_split_kernel<<<(unsigned)(152 * 8), kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs, mid,
-                                                                     ws.info);
-        ++g_launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        mid_leaf_kernel<<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.xs, mid, ws.info);
-        ++g_launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    } else {
-        leaf_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, t.leaf_cell, ws.xs,
-                                                                         ws.info);
-        ++g_launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    big_leaf_kernel<MODE><<<152, kBigThreads, 0, s>>>(T, o, ws.xs, ws.info);
-    ++g_launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mark(ws, "leaves", s);
     for (int d = kDepthMax - 1; d >= 0; --d) {
         level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.info, d);
         ++g_launches;
@@ -317,7 +505,38 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// xs[k] = xm[perm[k]]: the particles in key order, for the tree walk when
+// the moments did not write them; every thread keeps four gathers in flight.
+__global__ void __launch_bounds__(256)
+    gather_records_kernel(const int32_t *__restrict__ perm, const float4 *__restrict__ xm,
+                          float4 *__restrict__ xs, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n / 4;
+    const int4 *p4 = reinterpret_cast<const int4 *>(perm);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += stride) {
+        const int4 id = __ldcs(p4 + g);
+        const float4 a = __ldg(xm + id.x), b = __ldg(xm + id.y), c = __ldg(xm + id.z),
+                     d = __ldg(xm + id.w);
+        xs[4 * g] = a;
+        xs[4 * g + 1] = b;
+        xs[4 * g + 2] = c;
+        xs[4 * g + 3] = d;
+    }
+    for (int64_t k = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+        xs[k] = __ldg(xm + perm[k]);
+}
+
 }  // namespace
+
+cudaError_t launch_gather_records(const int32_t *perm, const float4 *xm, float4 *xs, int64_t n,
+                                  cudaStream_t s) {
+    int64_t g = (n / 4 + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    gather_records_kernel<<<(unsigned)g, 256, 0, s>>>(perm, xm, xs, n);
+    ++g_launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_moments(tb_tree &t, Workspace &ws, int mode, cudaStream_t s) {
     switch (mode) {

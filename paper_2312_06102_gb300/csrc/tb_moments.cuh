@@ -324,10 +324,22 @@ __device__ void finish_split(const MomOut &o, int64_t c, const AccP &A, const Ac
     write_cell_f32(o, c, M, ch, cl, Q, bb);
 }
 
+// Records of the particles in key order read through the permutation:
+// src[k] = xm[perm[k]], the (x, y, z, m) of the k-th particle in key order
+// (Sec. 2.3 step 3) without writing the reordered array.
+struct PermSrc {
+    const float4 *__restrict__ xm;
+    const int32_t *__restrict__ perm;
+    __device__ __forceinline__ float4 operator[](int64_t k) const { return __ldg(xm + perm[k]); }
+};
+
 // A leaf of at most kSplitLeaf members in the compensated mode: two
-// interleaved plain FP32 accumulators (see kSplitLeaf).
-__device__ __forceinline__ void leaf_sum_split(const MomOut &o, const float4 *__restrict__ xs, int64_t c,
-                                               int64_t pf, int64_t pe) {
+// interleaved plain FP32 accumulators (see kSplitLeaf).  `xs` is any source
+// of key-ordered records indexed by position: a pointer (global or shared
+// memory) or a PermSrc.
+template <class Src>
+__device__ __forceinline__ void leaf_sum_split(const MomOut &o, Src xs, int64_t c, int64_t pf,
+                                               int64_t pe) {
     constexpr int G = 4;
     const float4 r0 = xs[pf];
     const float ref[3] = {r0.x, r0.y, r0.z};
@@ -362,9 +374,8 @@ __device__ __forceinline__ void leaf_sum_split(const MomOut &o, const float4 *__
 // are issued four at a time before any is used.  Leaves reaching this path
 // hold at most 2048 particles (longer ones, only possible at depth 21, go to
 // big_leaf_kernel), so the FP32 modes never need the FP64 route here.
-template <int MODE>
-__device__ void leaf_sum(const MomOut &o, const float4 *__restrict__ xs, int64_t c, int64_t pf,
-                         int64_t pe) {
+template <int MODE, class Src>
+__device__ void leaf_sum(const MomOut &o, Src xs, int64_t c, int64_t pf, int64_t pe) {
     constexpr int G = 4;
     const float4 r0 = xs[pf];
     const float ref[3] = {r0.x, r0.y, r0.z};
