@@ -668,6 +668,18 @@ def run_batched(a, tb, torch):
         raise RuntimeError(f"batched replay failed: {tb.STATUS[st]}")
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     batched_ms = float(np.median(ms))
+    # stage times of a few builds outside the graph (events at stage ends)
+    tree.profile(True)
+    tree.stage_times(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+    st_ = tree.stage_times(stream)
+    tree.profile(False)
+    stages = {}
+    for name, v in st_:
+        if name != "start":
+            stages[name] = stages.get(name, 0.0) + v / 3
 
     # plain loop: one tb_build + tb_moments per set, one tree rebuilt in place
     sizes = np.diff(b.offsets)
@@ -702,8 +714,62 @@ def run_batched(a, tb, torch):
             "plain_loop_mparticles_s": round(n / plain_ms / 1e3, 2),
             "speedup_vs_plain": round(plain_ms / batched_ms, 1),
             "kernels_per_batched_build": int(per_build),
+            "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "timing": "CUDA events around each graph replay (jitter kernel outside); plain loop: "
                       "events around the whole loop of per-set calls, no host sync inside"}
+
+
+def run_precision_batched(a):
+    """The batched workload's moment error per level, three modes, against the
+    oracle's FP64 direct sums over every cell of 64 sets spread over the size
+    range (each set is its own tree)."""
+    import torch
+    import oracle
+    import paper_2312_06102_gb300 as tb
+    spec = WORKLOADS["batched_4096"]
+    b = batched_plummer(n_sets=spec["n_sets"], seed=spec["seed"])
+    n_crit = a.n_crit or spec["n_crit"]
+    sizes = np.diff(b.offsets)
+    order = np.argsort(sizes, kind="stable")
+    pick = order[np.linspace(0, len(order) - 1, 64).astype(np.int64)]
+    p = torch.from_numpy(b.pos).cuda()
+    w = torch.from_numpy(b.mass).cuda()
+    off = torch.from_numpy(b.offsets).cuda()
+    ref = {}
+    for s_ in pick:
+        lo_, hi_ = int(b.offsets[s_]), int(b.offsets[s_ + 1])
+        o = oracle.build_tree(b.pos[lo_:hi_], n_crit)
+        M, com, quad, _ = oracle.moments(o, b.pos[lo_:hi_], b.mass[lo_:hi_])
+        ref[int(s_)] = (o.level.astype(np.int64), o.side, M, com, quad)
+    report = {"workload": "batched_4096", "sets_compared": len(pick),
+              "particles_compared": int(sizes[pick].sum()), "n_crit": n_crit, "levels": {}}
+    for mode, name in ((0, "fp32_comp"), (1, "fp32_plain"), (2, "fp64")):
+        t = tb.build_batched(p, w, off, n_crit=n_crit, mom_mode=mode)
+        torch.cuda.synchronize()
+        co = t.set_cell_offset.cpu().numpy()
+        gm_all = (t.mass64 if mode == 2 else t.mass).cpu().numpy()
+        gc_all = t.com64.cpu().numpy() if mode == 2 else (
+            t.com.cpu().numpy().astype(np.float64) + t.com_lo.cpu().numpy().astype(np.float64))
+        gq_all = (t.quad64 if mode == 2 else t.quad).cpu().numpy().astype(np.float64)
+        for s_, (lv, side, M, com, quad) in ref.items():
+            a0, a1 = int(co[s_]), int(co[s_ + 1])
+            assert a1 - a0 == len(lv)
+            sc = side / np.exp2(lv)
+            em = np.abs(gm_all[a0:a1].astype(np.float64) / M - 1)
+            ec = np.abs(gc_all[a0:a1] - com).max(1) / sc
+            eq = np.abs(gq_all[a0:a1] - quad).max(1) / (M * sc * sc)
+            for d in np.unique(lv):
+                k = lv == d
+                r = report["levels"].setdefault(int(d), {"cells": 0})
+                if mode == 0:
+                    r["cells"] += int(k.sum())
+                cur = r.setdefault(name, {"mass_rel": 0.0, "com_per_side": 0.0, "quad_per_Ms2": 0.0})
+                cur["mass_rel"] = max(cur["mass_rel"], float(em[k].max()))
+                cur["com_per_side"] = max(cur["com_per_side"], float(ec[k].max()))
+                cur["quad_per_Ms2"] = max(cur["quad_per_Ms2"], float(eq[k].max()))
+        t.free()
+    print(json.dumps(report), flush=True)
+    return 0
 
 
 def run_precision(a):
@@ -713,6 +779,8 @@ def run_precision(a):
     import oracle
     import paper_2312_06102_gb300 as tb
     wl = a.precision_workload
+    if WORKLOADS[wl]["kind"] == "batched":
+        return run_precision_batched(a)
     pos, mass, spec, n = gen(wl, a.n)
     n_crit = a.n_crit or spec["n_crit"]
     idx = oracle.PrefixIndex(pos)

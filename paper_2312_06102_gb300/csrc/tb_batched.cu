@@ -13,8 +13,9 @@
 //                         set's cell and leaf counts per level;
 //   batch_scan_kernel   : cell and leaf offsets of every set (set order);
 //   batch_emit_kernel   : persistent, one block per set: every cell with its
-//                         links (the single-tree emission, tile after tile with
-//                         running counts), then the set's particles in key order;
+//                         links (the single-tree emission from the m_k and L_k
+//                         the count stored, tile after tile with running
+//                         counts), then the set's particles in key order;
 //   batch_moments_kernel: persistent, one block per set: moments level by level,
 //                         deepest first, with a block barrier between levels.
 // The paper builds disjoint subtrees on dynamically scheduled threads
@@ -56,6 +57,7 @@ struct BatchArgs {
     int32_t *palt;
     float4 *xm;
     float4 *xs;
+    uint16_t *ml;             // [n] m_k | L_k << 8 of each sorted particle (count -> emit)
     uint32_t *set_cnt;        // [S][kLevelFields]
     int64_t *set_cell_off;    // [S+1]
     int64_t *set_leaf_off;    // [S+1]
@@ -270,7 +272,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_front_kernel(BatchArgs A) 
         __syncthreads();
         for (int64_t s = o; s < o + ns; s += kLvTile) {
             const int64_t e = min64(o + ns, s + kLvTile);
-            tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            const Front f = tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            if (f.k < e) A.ml[f.k] = (uint16_t)(f.m | (f.L << 8));
             warp_field_prefix(ts, nullptr, s_tile);
             __syncthreads();
             if (threadIdx.x < kLevelFields) s_tot[threadIdx.x] += s_tile[threadIdx.x];
@@ -334,9 +337,8 @@ __global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t c
     if (threadIdx.x == 0) A.info->max_depth = s_dmax;
 }
 
-__global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, EmitOut out) {
+__global__ void __launch_bounds__(kBThreads, 2) batch_emit_kernel(BatchArgs A, EmitOut out) {
     if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
-    extern __shared__ __align__(16) unsigned char raw[];
     __shared__ TileShared ts;
     __shared__ uint32_t woff[kLvWarps][kLevelFields];
     __shared__ uint32_t s_run[kLevelFields], s_lvl[kLevelFields], s_tile[kLevelFields];
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, E
         __syncthreads();
         for (int64_t s = o; s < o + ns; s += kLvTile) {
             const int64_t e = min64(o + ns, s + kLvTile);
-            const Front f = tile_front(A.pkey, o, o + ns, A.ncrit, s, e, raw, ts);
+            const Front f = tile_front_ml(A.ml, o, s, e, ts);
             warp_field_prefix(ts, woff, s_tile);
             if (threadIdx.x < kLevelFields) {
                 const int fld = threadIdx.x;
@@ -374,8 +376,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_emit_kernel(BatchArgs A, E
                 auto P = [&](int d) {
                     return ts.base[d] + woff[warp][d] + (uint32_t)__popc(ts.mask[warp][d] & lt);
                 };
-                const uint64_t K = reinterpret_cast<const uint64_t *>(raw)[f.k - (s - A.ncrit - 1)];
-                emit_particle(f, P, o, o + ns, K, out);
+                emit_particle(f, P, o, o + ns, A.pkey[f.k], out);
             }
             __syncthreads();
             if (threadIdx.x < kLevelFields) s_run[threadIdx.x] += s_tile[threadIdx.x];
@@ -474,18 +475,14 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                            int ncrit, tb_tree &t, Workspace &ws, int64_t cell_cap, int phase,
                            int mode, cudaStream_t s) {
     BatchArgs A{pos, mass, off, ws.set_order, S, ncrit, t.pkey, t.perm, ws.keys_alt,
-                ws.perm_alt, ws.xm, ws.xs, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
+                ws.perm_alt, ws.xm, ws.xs, ws.ml, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
                 t.set_root, ws.set_ctr, ws.info};
     cudaError_t e;
     static std::atomic<uint64_t> attr_done{0};
     if (first_on_device(attr_done)) {
         const int sm_front = (int)batch_front_smem(kMaxNcrit);
         cudaFuncSetAttribute(batch_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_front);
-        cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)lv_smem_bytes(kMaxNcrit));
         cudaFuncSetAttribute(batch_front_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(batch_emit_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     }
     int dev = 0, nsm = 152;
@@ -508,7 +505,8 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
     }
     EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
                 t.leaf_cell};
-    batch_emit_kernel<<<grid_big, kBThreads, lv_smem_bytes(ncrit), s>>>(A, out);
+    const int grid_emit = S < 2 * nsm ? (S > 0 ? S : 1) : 2 * nsm;
+    batch_emit_kernel<<<grid_emit, kBThreads, 0, s>>>(A, out);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark(ws, "batch_emit", s);

@@ -110,6 +110,27 @@ __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, 
     return f;
 }
 
+// The same Front from the m_k | L_k << 8 words a counting pass stored for
+// every particle (no keys needed): particle s + threadIdx.x of the tile
+// [s, e) of the tree [seg_lo, ...), and the level masks of every warp.
+__device__ Front tile_front_ml(const uint16_t *__restrict__ ml, int64_t seg_lo, int64_t s,
+                               int64_t e, TileShared &ts) {
+    Front f;
+    f.k = s + threadIdx.x;
+    if (f.k < e) {
+        const uint32_t v = ml[f.k];
+        f.m = (int)(v & 0xffu);
+        f.L = (int)(v >> 8);
+        f.Lprev = (f.k > seg_lo) ? (int)(ml[f.k - 1] >> 8) : 0;
+    } else {
+        f.m = 255;
+        f.L = 0;
+        f.Lprev = 0;
+    }
+    store_level_masks(f.m, f.L, ts);
+    __syncthreads();
+    return f;
+}
 
 // Per-field prefix over the 32 warps of a 1024-thread tile, one warp per
 // field (fields 0..22): woff[w][f] = starts of field f in warps before w;

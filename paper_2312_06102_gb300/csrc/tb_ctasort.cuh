@@ -26,7 +26,37 @@ struct CtaSortShared {
     uint32_t run[kCtaRadix];
     uint32_t tile_off[kCtaRadix + 1];
     uint32_t cnt[kCtaRadix];
+    uint32_t carry[kCtaRadix / 32];
 };
+
+// Exclusive prefix of the kCtaRadix counts in[] into out[] (out may alias
+// in), with the total in out[kCtaRadix] when out_total is set: eight warps,
+// 32 digits each, one shuffle scan per warp and a carry across warps.  All
+// threads of the block call it; it ends with a barrier.
+__device__ __forceinline__ void cta_digit_scan(const uint32_t *in, uint32_t *out, bool out_total,
+                                               uint32_t *s_carry /* [kCtaRadix / 32] */) {
+    static_assert(kCtaRadix == 256 && kCtaThreads >= kCtaRadix, "digit scan shape");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = 0, x = 0;
+    if (threadIdx.x < kCtaRadix) {
+        v = in[threadIdx.x];
+        x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_carry[warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kCtaRadix) {
+        uint32_t c = 0;
+        for (int w = 0; w < warp; ++w) c += s_carry[w];
+        out[threadIdx.x] = c + x - v;
+        if (out_total && threadIdx.x == kCtaRadix - 1) out[kCtaRadix] = c + x;
+    }
+    __syncthreads();
+}
 
 // Digit counts of every pass over [o, o + ns) into sm.hist.
 __device__ void cta_histograms(const uint64_t *keys, int64_t o, int64_t ns, int shift0, int passes,
@@ -54,10 +84,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
     int32_t *vsrc = vals, *vdst = alt_v;
     for (int p = 0; p < passes; ++p) {
         const int shift = shift0 + p * kCtaRadixBits;
-        if (threadIdx.x == 0) {
-            uint32_t r = 0;
-            for (int d = 0; d < kCtaRadix; ++d) { sm.run[d] = r; r += sm.hist[p][d]; }
-        }
+        cta_digit_scan(sm.hist[p], sm.run, false, sm.carry);
         for (int64_t tb = 0; tb < ns; tb += kCtaTile) {
             const int valid = (int)min64(kCtaTile, ns - tb);
             for (int i = threadIdx.x; i < kCtaWarps * (kCtaRadix + 1); i += blockDim.x)
@@ -112,12 +139,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
                 sm.cnt[d] = acc;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t r = 0;
-                for (int d = 0; d < kCtaRadix; ++d) { sm.tile_off[d] = r; r += sm.cnt[d]; }
-                sm.tile_off[kCtaRadix] = r;
-            }
-            __syncthreads();
+            cta_digit_scan(sm.cnt, sm.tile_off, true, sm.carry);
 #pragma unroll
             for (int i = 0; i < kCtaItems; ++i) {
                 const int e = wbase + i * 32 + lane;
