@@ -43,9 +43,9 @@ from synth import WORKLOADS, batched_plummer, workload  # noqa: E402
 # the digest of the kernel source it was taken on; reported only while the
 # source is unchanged (see profiles/).
 NCU_TRAFFIC = {
-    # onesweep pass <8, 512, 8>, N = 2^25 clustered, passes 2 and 3 of a timed
-    # build: dram__bytes_read.sum + dram__bytes_write.sum, mean of the two
-    "2d099ad8c5a312c4": {"bytes": 770.69e6, "n": 1 << 25, "variant": (8, 512, 8)},
+    # onesweep pass <8, 512, 8>, N = 2^25 clustered, passes 2, 3 and 4 of a
+    # timed build: dram__bytes_read.sum + dram__bytes_write.sum, their mean
+    "c2fc7b857da4a80b": {"bytes": 770.67e6, "n": 1 << 25, "variant": (8, 512, 8)},
 }
 
 METRIC = "tree-build Mparticles/s + HBM roofline %; batched vs plain on same GB300"
@@ -79,6 +79,8 @@ def args_():
     ap.add_argument("--keys", default="morton", choices=["morton", "hilbert"],
                     help="particle key order of the timed builds")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-sets", type=int, default=0,
+                    help="number of sets of the batched workload (default: its 4,096)")
     ap.add_argument("--precision", action="store_true",
                     help="print the per-level moment error of the three modes against the oracle")
     return ap.parse_args()
@@ -630,7 +632,7 @@ def run_batched(a, tb, torch):
     one tb_build + tb_moments per set, both timed with CUDA events."""
     spec = WORKLOADS["batched_4096"]
     t0 = time.perf_counter()
-    b = batched_plummer(n_sets=spec["n_sets"], seed=spec["seed"])
+    b = batched_plummer(n_sets=a.batched_sets or spec["n_sets"], seed=spec["seed"])
     log(f"[bench] generated batched_4096 ({int(b.offsets[-1])} particles) in {time.perf_counter() - t0:.1f}s")
     n = int(b.offsets[-1])
     S = len(b.offsets) - 1
@@ -705,7 +707,8 @@ def run_batched(a, tb, torch):
     plain_ms = e0.elapsed_time(e1) / loops
     if plain.sync() != 0:
         raise RuntimeError("plain loop failed")
-    return {"workload": "batched_4096", "sets": S, "particles": n, "n_crit": n_crit,
+    return {"workload": "batched_4096" if S == spec["n_sets"] else f"batched_{S}",
+            "sets": S, "particles": n, "n_crit": n_crit,
             "graph_replays": steps, "cell_capacity": cap,
             "batched_ms_per_build": round(batched_ms, 4),
             "batched_mparticles_s": round(n / batched_ms / 1e3, 1),
