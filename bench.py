@@ -79,6 +79,8 @@ def args_():
     ap.add_argument("--keys", default="morton", choices=["morton", "hilbert"],
                     help="particle key order of the timed builds")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batch-threads", type=int, default=0, choices=[0, 512, 1024],
+                    help="threads per set of the batched build (default: tuned)")
     ap.add_argument("--batched-sets", type=int, default=0,
                     help="number of sets of the batched workload (default: its 4,096)")
     ap.add_argument("--precision", action="store_true",
@@ -641,17 +643,27 @@ def run_batched(a, tb, torch):
     w = torch.from_numpy(b.mass).cuda()
     off = torch.from_numpy(b.offsets).cuda()
     jit = Jitter(torch, b, spec["seed"])
-    tree = tb.build_batched(p, w, off, n_crit=n_crit)
+    # the block size per set (512 or 1024 threads), tuned untimed unless named
+    bt, bt_ms = 0, None
+    if a.batch_threads:
+        bt = a.batch_threads
+    elif not a.no_autotune:
+        from paper_2312_06102_gb300 import autotune
+        bt, bt_ms = autotune.tune_batched(p, w, off, n_crit=n_crit)
+        log(f"[bench] batched autotune: {bt} " + " ".join(f"{k}:{v:.3f}" for k, v in bt_ms.items()))
+    tree = tb.build_batched(p, w, off, n_crit=n_crit, batch_threads=bt)
     cap = int(tree.n_cells * 1.1) + 1024
     stream = torch.cuda.Stream()
     g_build = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
-        tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+        tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream,
+                         batch_threads=bt)
         jit.fill(0, p)
         stream.synchronize()
         l0 = tb.kernel_launches()
         with torch.cuda.graph(g_build, stream=stream):
-            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream,
+                             batch_threads=bt)
         per_build = tb.kernel_launches() - l0
     steps = a.batched_steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -675,7 +687,8 @@ def run_batched(a, tb, torch):
     tree.stage_times(stream)
     with torch.cuda.stream(stream):
         for _ in range(3):
-            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream)
+            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream,
+                             batch_threads=bt)
     st_ = tree.stage_times(stream)
     tree.profile(False)
     stages = {}
@@ -717,6 +730,9 @@ def run_batched(a, tb, torch):
             "plain_loop_mparticles_s": round(n / plain_ms / 1e3, 2),
             "speedup_vs_plain": round(plain_ms / batched_ms, 1),
             "kernels_per_batched_build": int(per_build),
+            "batch_threads": int(bt) if bt else 512,
+            "batch_threads_autotune_ms": ({str(k): round(v, 3) for k, v in bt_ms.items()}
+                                          if bt_ms else None),
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "timing": "CUDA events around each graph replay (jitter kernel outside); plain loop: "
                       "events around the whole loop of per-set calls, no host sync inside"}

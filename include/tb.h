@@ -99,8 +99,9 @@ typedef struct {
     int32_t sort_threads;    /* 0 = tuned default; else threads per sort tile; tb_build only */
     int32_t sort_items;      /* 0 = tuned default; else keys per thread of a sort tile
                                 (compiled variants: see tb_sort_variant); tb_build only */
-    int32_t batch_threads;   /* reserved: the batched build runs one 1024-thread block
-                                per set, whatever the value */
+    int32_t batch_threads;   /* tb_build_batched only: threads of the block that builds
+                                one set, 512 (two sets per SM at a time; the default
+                                for 0) or 1024 (one) */
     int32_t key_order;       /* tb_key_order: TB_KEYS_MORTON (default) or TB_KEYS_HILBERT
                                 (tb_build only; tb_build_batched takes Morton keys) */
 } tb_params;
@@ -191,10 +192,10 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
  * params.cell_capacity > 0 and a tree from an earlier call with the same S
  * and n_total, nothing is allocated and nothing synchronises, so the call can
  * be captured into a CUDA graph and replayed.
- * Of params it reads n_crit, mom_mode and cell_capacity; key_order must be
- * TB_KEYS_MORTON.  Its shape is fixed (one 1024-thread block per set, five
- * 8-bit sort passes over the upper 40 key bits), so radix_bits,
- * sort_threads, sort_items, batch_threads and reorder are not used. */
+ * Of params it reads n_crit, mom_mode, cell_capacity and batch_threads;
+ * key_order must be TB_KEYS_MORTON.  Each set is sorted by one block (five
+ * 8-bit passes over the upper 40 key bits, then its runs of equal upper
+ * bits), so radix_bits, sort_threads, sort_items and reorder are not used. */
 tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_t *d_set_offsets,
                            int32_t n_sets, int64_t n_total, const tb_params *params,
                            tb_stream stream, tb_tree **tree);

@@ -285,6 +285,10 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
     if set_offsets.dtype != torch.int64 or not set_offsets.is_cuda:
         raise ValueError("set_offsets must be an int64 CUDA tensor")
     t = tree if tree is not None else Tree()
+    if not batch_threads:
+        from . import autotune
+        batch_threads = autotune.cached_batched(set_offsets.shape[0] - 1,
+                                                pos.shape[0] if n_total is None else n_total) or 0
     p = _params(n_crit, mom_mode, cell_capacity, 0, radix_bits, batch_threads)
     p.key_order = int(key_order)
     n_total = pos.shape[0] if n_total is None else n_total

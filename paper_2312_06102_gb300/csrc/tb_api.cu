@@ -209,6 +209,7 @@ bool valid_params(const tb_params *p) {
            p->cell_capacity >= 0 && p->cell_capacity <= kMaxCells &&
            (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11)) &&
            (p->key_order == TB_KEYS_MORTON || p->key_order == TB_KEYS_HILBERT) &&
+           batch_threads_valid(p->batch_threads) &&
            sort_cfg_valid(pick_cfg(p));
 }
 
@@ -479,8 +480,9 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
     mark(ws, "start", s);
     e = launch_set_check(t.set_particle_offset, n_sets, n_total, ws, s);
     if (e == cudaSuccess)
-        e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit, t, ws,
-                           params->cell_capacity, 0, params->mom_mode, s);
+        e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit,
+                           params->batch_threads, t, ws, params->cell_capacity, 0,
+                           params->mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
     if (params->cell_capacity == 0) {
         st = read_info(*S, s);
@@ -492,8 +494,8 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
                           params->mom_mode == TB_MOM_FP64);
         if (st != TB_OK) return st;
     }
-    e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit, t, ws,
-                       params->cell_capacity, 1, params->mom_mode, s);
+    e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit,
+                       params->batch_threads, t, ws, params->cell_capacity, 1, params->mom_mode, s);
     if (e != cudaSuccess) return from_cuda(e);
     if (params->cell_capacity == 0) {
         st = read_info(*S, s);

@@ -19,9 +19,11 @@ __host__ __device__ inline int lv_pow2(int ncrit) {
     return p;
 }
 
+// Shared memory of tile_front for tiles of T particles.
+template <int T = kLvTile>
 __host__ __device__ inline size_t lv_smem_bytes(int ncrit) {
-    size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;   // keys of [s-n-1, e+n)
-    size_t nc = (size_t)kLvTile + ncrit + 1;                // c over [s-n-1, e)
+    size_t ext = (size_t)T + 2 * (size_t)ncrit + 1;   // keys of [s-n-1, e+n)
+    size_t nc = (size_t)T + ncrit + 1;                // c over [s-n-1, e)
     return ((ext * 8 + 15) & ~size_t(15)) + 2 * ((nc + 15) & ~size_t(15)) + 64;
 }
 
@@ -30,18 +32,22 @@ struct Front {
     int64_t k;
 };
 
-// Shared state of one tile: masks and counts per warp and field
-// (fields 0..21 = cell starts per level, 22 = leaf starts).
-struct TileShared {
-    uint32_t mask[kLvWarps][kLevelFields];
+// Shared state of one tile of T particles (one per thread): masks and counts
+// per warp and field (fields 0..21 = cell starts per level, 22 = leaf starts).
+template <int T>
+struct TileSharedT {
+    static constexpr int WARPS = T / 32;
+    uint32_t mask[WARPS][kLevelFields];
     uint32_t base[kLevelFields];
 };
+using TileShared = TileSharedT<kLvThreads>;
 
 // Per-warp masks of the lanes starting a cell at each level (fields 0..21)
 // and of the lanes starting a leaf (field 22).  Each lane holds the interval
 // [m, L] as a row of bits; a 32 x 32 bit-matrix transpose across the warp
 // (five exchange rounds) leaves in lane d the mask of field d.
-__device__ __forceinline__ void store_level_masks(int m, int L, TileShared &ts) {
+template <int T>
+__device__ __forceinline__ void store_level_masks(int m, int L, TileSharedT<T> &ts) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = (m <= L) ? (((2u << L) - (1u << m)) | (1u << kLevels)) : 0u;
     uint32_t msk = 0x0000ffffu;
@@ -59,22 +65,23 @@ __device__ __forceinline__ void store_level_masks(int m, int L, TileShared &ts) 
 // tile lies in the segment [seg_lo, seg_hi) of sorted keys that forms one
 // tree (the whole array, or one set of a batch); keys outside it do not
 // exist for this tree.
+template <int T>
 __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, int64_t seg_hi,
-                            int ncrit, int64_t s, int64_t e, unsigned char *raw, TileShared &ts) {
+                            int ncrit, int64_t s, int64_t e, unsigned char *raw, TileSharedT<T> &ts) {
     const int64_t lo = s - ncrit - 1;
     const int next = (int)(e + ncrit - lo);
     const int nc = (int)(e - lo);
-    const size_t ext = (size_t)kLvTile + 2 * (size_t)ncrit + 1;
-    const size_t ncp = ((size_t)kLvTile + ncrit + 1 + 15) & ~size_t(15);
+    const size_t ext = (size_t)T + 2 * (size_t)ncrit + 1;
+    const size_t ncp = ((size_t)T + ncrit + 1 + 15) & ~size_t(15);
     uint64_t *key = reinterpret_cast<uint64_t *>(raw);
     uint8_t *A = raw + ((ext * 8 + 15) & ~size_t(15));
     uint8_t *B = A + ncp;
-    for (int x = threadIdx.x; x < next; x += blockDim.x) {
+    for (int x = threadIdx.x; x < next; x += T) {
         const int64_t i = lo + x;
         key[x] = (i >= seg_lo && i < seg_hi) ? skeys[i] : 0ull;
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < nc; x += blockDim.x) {
+    for (int x = threadIdx.x; x < nc; x += T) {
         const int64_t i = lo + x;
         int v = 0;
         if (i >= seg_lo && i + ncrit < seg_hi) v = min(kDepthMax, min_depth(key[x], key[x + ncrit]));
@@ -83,7 +90,7 @@ __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, 
     __syncthreads();
     const int p = lv_pow2(ncrit);
     for (int q = 1; q < p; q *= 2) {
-        for (int x = threadIdx.x; x < nc; x += blockDim.x)
+        for (int x = threadIdx.x; x < nc; x += T)
             B[x] = (x + q < nc) ? max(A[x], A[x + q]) : A[x];
         __syncthreads();
         uint8_t *t = A; A = B; B = t;
@@ -113,8 +120,9 @@ __device__ Front tile_front(const uint64_t *__restrict__ skeys, int64_t seg_lo, 
 // The same Front from the m_k | L_k << 8 words a counting pass stored for
 // every particle (no keys needed): particle s + threadIdx.x of the tile
 // [s, e) of the tree [seg_lo, ...), and the level masks of every warp.
+template <int T>
 __device__ Front tile_front_ml(const uint16_t *__restrict__ ml, int64_t seg_lo, int64_t s,
-                               int64_t e, TileShared &ts) {
+                               int64_t e, TileSharedT<T> &ts) {
     Front f;
     f.k = s + threadIdx.x;
     if (f.k < e) {
@@ -132,22 +140,25 @@ __device__ Front tile_front_ml(const uint16_t *__restrict__ ml, int64_t seg_lo, 
     return f;
 }
 
-// Per-field prefix over the 32 warps of a 1024-thread tile, one warp per
-// field (fields 0..22): woff[w][f] = starts of field f in warps before w;
-// tot[f] = the tile's total.  Needs a barrier before (masks written) and
-// after (results read).
-__device__ __forceinline__ void warp_field_prefix(const TileShared &ts,
+// Per-field prefix over the warps of a tile, one warp per field (fields
+// 0..22, taken in turns when the tile has fewer than 23 warps), one lane per
+// warp of the tile: woff[w][f] = starts of field f in warps before w; tot[f] =
+// the tile's total.  Needs a barrier before (masks written) and after
+// (results read).
+template <int T>
+__device__ __forceinline__ void warp_field_prefix(const TileSharedT<T> &ts,
                                                   uint32_t (*woff)[kLevelFields], uint32_t *tot) {
-    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
-    if (f < kLevelFields) {
-        const uint32_t v = __popc(ts.mask[lane][f]);
+    constexpr int W = TileSharedT<T>::WARPS;
+    const int lane = threadIdx.x & 31;
+    for (int f = threadIdx.x >> 5; f < kLevelFields; f += W) {
+        const uint32_t v = lane < W ? __popc(ts.mask[lane][f]) : 0u;
         uint32_t x = v;
 #pragma unroll
         for (int sh = 1; sh < 32; sh <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, sh);
             if (lane >= sh) x += y;
         }
-        if (woff) woff[lane][f] = x - v;
+        if (woff && lane < W) woff[lane][f] = x - v;
         if (lane == 31) tot[f] = x;
     }
 }

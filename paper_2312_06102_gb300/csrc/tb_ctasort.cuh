@@ -1,8 +1,8 @@
 // tb_ctasort.cuh -- a stable LSD radix sort of one contiguous range of
-// (64-bit key, 32-bit value) pairs by a single 1024-thread block: every pass
-// takes the range's tiles in order with running per-digit offsets, so it
-// needs no coordination with other blocks.  Used for the sets of a batched
-// build and for the rare long runs left by the single-tree sort.
+// (64-bit key, 32-bit value) pairs by a single block of T threads (T = 512 or
+// 1024): every pass takes the range's tiles in order with running per-digit
+// offsets, so it needs no coordination with other blocks.  Used for the sets
+// of a batched build and for the rare long runs left by the single-tree sort.
 #pragma once
 
 #include "tb_device.cuh"
@@ -10,32 +10,35 @@
 namespace tb {
 namespace {
 
-constexpr int kCtaThreads = 1024;
-constexpr int kCtaWarps = kCtaThreads / 32;
+constexpr int kCtaThreads = 1024;                // block of the long-run sort
 constexpr int kCtaRadixBits = 8;
 constexpr int kCtaRadix = 1 << kCtaRadixBits;
 constexpr int kCtaMaxPasses = 8;
 constexpr int kCtaItems = 4;                     // keys per thread of a tile
-constexpr int kCtaTile = kCtaThreads * kCtaItems;
 
-struct CtaSortShared {
-    uint64_t keys[kCtaTile];
-    int32_t vals[kCtaTile];
-    uint32_t warp_hist[kCtaWarps][kCtaRadix + 1];
+template <int T>
+struct CtaSortSharedT {
+    static constexpr int WARPS = T / 32;
+    static constexpr int TILE = T * kCtaItems;
+    uint64_t keys[TILE];
+    int32_t vals[TILE];
+    uint32_t warp_hist[WARPS][kCtaRadix + 1];
     uint32_t hist[kCtaMaxPasses][kCtaRadix];
     uint32_t run[kCtaRadix];
     uint32_t tile_off[kCtaRadix + 1];
     uint32_t cnt[kCtaRadix];
     uint32_t carry[kCtaRadix / 32];
 };
+using CtaSortShared = CtaSortSharedT<kCtaThreads>;
 
 // Exclusive prefix of the kCtaRadix counts in[] into out[] (out may alias
 // in), with the total in out[kCtaRadix] when out_total is set: eight warps,
 // 32 digits each, one shuffle scan per warp and a carry across warps.  All
 // threads of the block call it; it ends with a barrier.
+template <int T>
 __device__ __forceinline__ void cta_digit_scan(const uint32_t *in, uint32_t *out, bool out_total,
                                                uint32_t *s_carry /* [kCtaRadix / 32] */) {
-    static_assert(kCtaRadix == 256 && kCtaThreads >= kCtaRadix, "digit scan shape");
+    static_assert(kCtaRadix == 256 && T >= kCtaRadix, "digit scan shape");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t v = 0, x = 0;
     if (threadIdx.x < kCtaRadix) {
@@ -59,11 +62,12 @@ __device__ __forceinline__ void cta_digit_scan(const uint32_t *in, uint32_t *out
 }
 
 // Digit counts of every pass over [o, o + ns) into sm.hist.
+template <int T>
 __device__ void cta_histograms(const uint64_t *keys, int64_t o, int64_t ns, int shift0, int passes,
-                               CtaSortShared &sm) {
-    for (int i = threadIdx.x; i < kCtaMaxPasses * kCtaRadix; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+                               CtaSortSharedT<T> &sm) {
+    for (int i = threadIdx.x; i < kCtaMaxPasses * kCtaRadix; i += T) (&sm.hist[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x) {
+    for (int64_t i = o + threadIdx.x; i < o + ns; i += T) {
         const uint64_t k = keys[i];
         for (int p = 0; p < passes; ++p)
             atomicAdd(&sm.hist[p][(k >> (shift0 + p * kCtaRadixBits)) & (kCtaRadix - 1)], 1u);
@@ -76,18 +80,21 @@ __device__ void cta_histograms(const uint64_t *keys, int64_t o, int64_t ns, int 
 // (keys, vals) -> (alt_k, alt_v) -> ...; with index_vals the first pass takes
 // each element's own position as its value.  Returns the number of passes
 // (the result is in alt_k / alt_v when it is odd).
+template <int T>
 __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v,
                             int64_t o, int64_t ns, int shift0, int passes, bool index_vals,
-                            CtaSortShared &sm) {
+                            CtaSortSharedT<T> &sm) {
+    constexpr int kCtaWarps = CtaSortSharedT<T>::WARPS;
+    constexpr int kCtaTile = CtaSortSharedT<T>::TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *src = keys, *dst = alt_k;
     int32_t *vsrc = vals, *vdst = alt_v;
     for (int p = 0; p < passes; ++p) {
         const int shift = shift0 + p * kCtaRadixBits;
-        cta_digit_scan(sm.hist[p], sm.run, false, sm.carry);
+        cta_digit_scan<T>(sm.hist[p], sm.run, false, sm.carry);
         for (int64_t tb = 0; tb < ns; tb += kCtaTile) {
             const int valid = (int)min64(kCtaTile, ns - tb);
-            for (int i = threadIdx.x; i < kCtaWarps * (kCtaRadix + 1); i += blockDim.x)
+            for (int i = threadIdx.x; i < kCtaWarps * (kCtaRadix + 1); i += T)
                 (&sm.warp_hist[0][0])[i] = 0;
             __syncthreads();
             uint64_t key[kCtaItems];
@@ -129,7 +136,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
                 rank[i] = __shfl_sync(0xffffffffu, oldc[i], lr[i] & 31u) + (lr[i] >> 8);
             __syncthreads();
             // warp offsets within each digit, tile digit counts
-            for (int d = threadIdx.x; d < kCtaRadix; d += blockDim.x) {
+            for (int d = threadIdx.x; d < kCtaRadix; d += T) {
                 uint32_t acc = 0;
                 for (int w = 0; w < kCtaWarps; ++w) {
                     const uint32_t c = sm.warp_hist[w][d];
@@ -139,7 +146,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
                 sm.cnt[d] = acc;
             }
             __syncthreads();
-            cta_digit_scan(sm.cnt, sm.tile_off, true, sm.carry);
+            cta_digit_scan<T>(sm.cnt, sm.tile_off, true, sm.carry);
 #pragma unroll
             for (int i = 0; i < kCtaItems; ++i) {
                 const int e = wbase + i * 32 + lane;
@@ -151,7 +158,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
                 }
             }
             __syncthreads();
-            for (int j = threadIdx.x; j < valid; j += blockDim.x) {
+            for (int j = threadIdx.x; j < valid; j += T) {
                 const uint64_t k = sm.keys[j];
                 const uint32_t d = (uint32_t)((k >> shift) & (kCtaRadix - 1));
                 const int64_t to = o + sm.run[d] + (j - sm.tile_off[d]);
@@ -159,7 +166,7 @@ __device__ int cta_lsd_sort(uint64_t *keys, int32_t *vals, uint64_t *alt_k, int3
                 vdst[to] = sm.vals[j];
             }
             __syncthreads();
-            for (int d = threadIdx.x; d < kCtaRadix; d += blockDim.x) sm.run[d] += sm.cnt[d];
+            for (int d = threadIdx.x; d < kCtaRadix; d += T) sm.run[d] += sm.cnt[d];
             __syncthreads();
         }
         uint64_t *t = src; src = dst; dst = t;

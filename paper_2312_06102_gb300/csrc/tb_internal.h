@@ -148,8 +148,9 @@ const SortCfg *sort_variant(int i);
 bool sort_cfg_valid(const SortCfg &c);
 
 cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *off, int32_t S,
-                           int ncrit, tb_tree &t, Workspace &ws, int64_t cell_cap, int phase,
-                           int mode, cudaStream_t s);
+                           int ncrit, int threads, tb_tree &t, Workspace &ws, int64_t cell_cap,
+                           int phase, int mode, cudaStream_t s);
+bool batch_threads_valid(int threads);   // 0 (default), 512 or 1024
 cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Workspace &ws,
                              cudaStream_t s);
 

@@ -152,3 +152,11 @@ def test_wait_limit_setter(tb):
     assert tb.lib().tb_set_wait_limit(-1) == EINVAL
     assert tb.lib().tb_set_wait_limit(5) == 0
     assert tb.lib().tb_set_wait_limit(0) == 0      # back to the default
+
+
+@pytest.mark.parametrize("threads", [-1, 1, 256, 768, 2048])
+def test_batched_rejects_block_sizes(tb, threads):
+    p = _params(tb, batch_threads=threads)
+    out = C.POINTER(tb.TreeC)()
+    code = tb.lib().tb_build_batched(16, None, 16, 1, 10, C.byref(p), None, C.byref(out))
+    assert code == EINVAL and not out

@@ -12,12 +12,13 @@ pytestmark = pytest.mark.gpu
 from gpu_util import TOL_COM, TOL_MASS, TOL_QUAD, tb, to_np, torch  # noqa: E402
 
 
-def _run(pos, mass, offsets, n_crit=16, cap=0, mode=0, tree=None):
+def _run(pos, mass, offsets, n_crit=16, cap=0, mode=0, tree=None, threads=512):
     m = tb()
     p = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).cuda()
     w = None if mass is None else torch.from_numpy(np.ascontiguousarray(mass, np.float32)).cuda()
     off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
-    t = m.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, mom_mode=mode, tree=tree)
+    t = m.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, mom_mode=mode, tree=tree,
+                        batch_threads=threads)
     torch.cuda.synchronize()
     assert t.sync() == 0
     return t, p, w, off
@@ -80,12 +81,27 @@ def _sets(sizes, seed):
     return pos, mass, offsets
 
 
-@pytest.mark.parametrize("n_crit", [1, 8, 16])
-def test_batched_mixed_sizes(n_crit):
-    sizes = [0, 1, 2, 16, 17, 100, 4095, 4096, 4097, 9000, 0, 3, 20_000, 65_536, 5]
+@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("n_crit", [1, 8, 16, 100])
+def test_batched_mixed_sizes(n_crit, threads):
+    """Both block sizes per set: tiles of 512 or 1024 particles, sort tiles of
+    2048 or 4096 keys; sizes around every tile boundary."""
+    sizes = [0, 1, 2, 16, 17, 100, 511, 512, 513, 1023, 1024, 1025, 2047, 2048, 2049, 4095,
+             4096, 4097, 9000, 0, 3, 20_000, 65_536, 5]
     pos, mass, offsets = _sets(sizes, 10 + n_crit)
-    t, *_ = _run(pos, mass, offsets, n_crit=n_crit)
+    t, *_ = _run(pos, mass, offsets, n_crit=n_crit, threads=threads)
     _check_sets(t, pos, mass, offsets, n_crit)
+
+
+def test_batched_block_sizes_agree():
+    """512- and 1024-thread builds of the same sets give identical arrays."""
+    sizes = [700, 3000, 50_000, 1, 9999]
+    pos, mass, offsets = _sets(sizes, 5)
+    a, *_ = _run(pos, mass, offsets, threads=512)
+    b, *_ = _run(pos, mass, offsets, threads=1024)
+    for k in ("pkey", "perm", "ckey", "level", "parent", "child_first", "child_end", "pfirst",
+              "pend", "mass", "com", "com_lo", "quad", "aabb"):
+        assert np.array_equal(to_np(getattr(a, k)), to_np(getattr(b, k))), k
 
 
 def test_batched_null_mass_and_fp64_mode():
