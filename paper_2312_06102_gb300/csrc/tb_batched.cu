@@ -507,7 +507,7 @@ cudaError_t launch_batched_t(const BatchArgs &A, int32_t S, int ncrit, tb_tree &
         return cudaSuccess;
     }
     EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-                t.leaf_cell};
+                t.leaf_cell, nullptr};
     // the emission keeps 1024-thread tiles whatever the front's block size
     // (two blocks per SM at 32 registers): measured faster than 512 (0.96
     // against 1.10 ms on the 4,096-set workload)

@@ -298,12 +298,16 @@ constexpr int kEfChunks = kEfTile / 32;
 
 __global__ void __launch_bounds__(kEfThreads, 2)
     emit_starts_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
-                       const uint32_t *__restrict__ tile_off, int64_t n_tiles, const DevInfo *info,
+                       const uint32_t *__restrict__ tile_off, int64_t n_tiles, DevInfo *info_w,
                        EmitOut out) {
+    const DevInfo *info = info_w;
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
     __shared__ uint32_t s_entry[kEfTile];               // k - s | m << 11 | L << 16 | Lprev << 21
     __shared__ uint32_t s_mask[kEfChunks][kLevels];     // level masks of each chunk of 32 starts
     __shared__ uint32_t s_cpre[kEfChunks][kLevels];     // starts of each level in earlier chunks
+    __shared__ uint32_t s_imask[kEfChunks][kLevels];    // the same for non-leaf cells (d < L)
+    __shared__ uint32_t s_ipre[kEfChunks][kLevels];
+    __shared__ uint32_t s_ibase[kLevels];               // the block's first slot in each level's list
     __shared__ uint32_t s_base[kLevelFields];           // first level-d cell (leaf) of the block
     __shared__ uint32_t s_wcnt[kEfWarps];
     __shared__ uint8_t s_Llast[kEfThreads];
@@ -371,15 +375,10 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __syncthreads();
     const int total = (int)s_total;
     const int nchunks = (total + 31) / 32;
-    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose)
-    for (int c = warp; c < nchunks; c += kEfWarps) {
-        const int i = c * 32 + lane;
-        uint32_t v = 0;
-        if (i < total) {
-            const uint32_t en = s_entry[i];
-            const uint32_t mm = (en >> 11) & 31u, LL = (en >> 16) & 31u;
-            v = (2u << LL) - (1u << mm);
-        }
+    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose): of
+    // the cells each start opens (levels m..L), and of the non-leaf ones
+    // among them (levels m..L-1)
+    auto transpose = [&](uint32_t v) {
         uint32_t msk = 0x0000ffffu;
 #pragma unroll
         for (int j = 16; j > 0; j >>= 1, msk ^= msk << j) {
@@ -387,15 +386,36 @@ __global__ void __launch_bounds__(kEfThreads, 2)
             if (lane & j) v ^= ((y >> j) ^ v) & msk;
             else v ^= (((v >> j) ^ y) & msk) << j;
         }
-        if (lane < kLevels) s_mask[c][lane] = v;
+        return v;
+    };
+    for (int c = warp; c < nchunks; c += kEfWarps) {
+        const int i = c * 32 + lane;
+        uint32_t v = 0, vi = 0;
+        if (i < total) {
+            const uint32_t en = s_entry[i];
+            const uint32_t mm = (en >> 11) & 31u, LL = (en >> 16) & 31u;
+            v = (2u << LL) - (1u << mm);
+            vi = (1u << LL) - (1u << mm);
+        }
+        v = transpose(v);
+        vi = transpose(vi);
+        if (lane < kLevels) {
+            s_mask[c][lane] = v;
+            s_imask[c][lane] = vi;
+        }
     }
     __syncthreads();
     if (threadIdx.x < kLevels) {
-        uint32_t r = 0;
+        uint32_t r = 0, ri = 0;
         for (int c = 0; c < nchunks; ++c) {
             s_cpre[c][threadIdx.x] = r;
             r += __popc(s_mask[c][threadIdx.x]);
+            s_ipre[c][threadIdx.x] = ri;
+            ri += __popc(s_imask[c][threadIdx.x]);
         }
+        // the block's slots in the level's list of non-leaf cells (their
+        // order in the list is immaterial: each is combined on its own)
+        s_ibase[threadIdx.x] = ri ? atomicAdd(&info_w->int_cnt[threadIdx.x], ri) : 0u;
     }
     __syncthreads();
     const unsigned lt = lanemask_lt();
@@ -422,6 +442,9 @@ __global__ void __launch_bounds__(kEfThreads, 2)
             out.pfirst[idx] = (int32_t)k;
             out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == mm ? 1 : 0);
             out.child_first[idx] = (d < LL) ? (int32_t)P(d + 1) : -1;
+            if (d < LL)
+                out.int_list[info->level_offset[d] + s_ibase[d] + s_ipre[c][d] +
+                             (uint32_t)__popc(s_imask[c][d] & lt)] = (int32_t)idx;
         }
         out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)P(LL);
     }
@@ -472,7 +495,7 @@ cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int ncrit, Workspace &
     (void)ncrit;
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
     EmitOut o{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-              t.leaf_cell};
+              t.leaf_cell, ws.int_list};
     const int64_t blocks = (n + kEfTile - 1) / kEfTile;
     emit_starts_kernel<<<(unsigned)blocks, kEfThreads, 0, s>>>(skeys, ws.ml, n, ws.level_cnt, tiles,
                                                                ws.info, o);

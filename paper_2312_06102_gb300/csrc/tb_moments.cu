@@ -11,9 +11,9 @@
 //                          through the permutation;
 //   big_leaf_kernel      : depth-21 leaves of identical keys that are too long
 //                          for one thread, summed block-wide;
-//   level_moments_kernel : one launch per level, deepest first: every other
-//                          cell combines its children, which earlier launches
-//                          finished.
+//   level_moments_kernel : one launch per level, deepest first: every non-leaf
+//                          cell (listed per level by the emission) combines
+//                          its children, which earlier launches finished.
 //
 // Moments of a cell: M = sum m; centre of mass c = sum m x / M; central
 // second moment Q = sum m (x - c)(x - c)^T (6 components xx xy xz yy yz zz);
@@ -301,30 +301,18 @@ __global__ void __launch_bounds__(kMomThreads, 4)
 }
 
 // The non-leaf cells of level d, from their children (finished by the
-// launch for level d + 1, or by the leaf launches).  Each warp takes 64
-// consecutive cells and packs their non-leaf ones, in order, onto its lanes.
+// launch for level d + 1, or by the leaf launches).  The emission listed
+// them per level, so every lane takes one.
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads, 4)
-    level_moments_kernel(TreeIn T, MomOut o, DevInfo *info, int d) {
+    level_moments_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ int_list, DevInfo *info,
+                         int d) {
     if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    __shared__ int32_t s_list[kMomThreads / 32][64];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t lo = info->level_offset[d], hi = info->level_offset[d + 1];
-    const int64_t nwarps = (int64_t)gridDim.x * (kMomThreads / 32);
-    const unsigned lt = lanemask_lt();
-    for (int64_t base = lo + ((int64_t)blockIdx.x * (kMomThreads / 32) + warp) * 64; base < hi;
-         base += nwarps * 64) {
-        const int64_t c0 = base + lane, c1 = base + 32 + lane;
-        const bool p0 = c0 < hi && T.child_first[c0] >= 0;
-        const bool p1 = c1 < hi && T.child_first[c1] >= 0;
-        const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
-        if (p0) s_list[warp][__popc(b0 & lt)] = (int32_t)c0;
-        if (p1) s_list[warp][__popc(b0) + __popc(b1 & lt)] = (int32_t)c1;
-        __syncwarp();
-        const int cnt = __popc(b0) + __popc(b1);
-        for (int k = lane; k < cnt; k += 32) combine_children<MODE>(T, o, s_list[warp][k]);
-        __syncwarp();
-    }
+    const int64_t cnt = info->int_cnt[d];
+    const int32_t *list = int_list + info->level_offset[d];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < cnt; q += stride)
+        combine_children<MODE>(T, o, list[q]);
 }
 
 // Block-wide sums of the long depth-21 leaves queued by the leaf launch.
@@ -497,7 +485,8 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
     for (int d = kDepthMax - 1; d >= 0; --d) {
-        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.info, d);
+        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.int_list,
+                                                                           ws.info, d);
         ++g_launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
