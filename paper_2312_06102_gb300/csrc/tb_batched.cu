@@ -16,8 +16,9 @@
 //                         links (the single-tree emission from the m_k and L_k
 //                         the count stored, tile after tile with running
 //                         counts), then the set's particles in key order;
-//   batch_moments_kernel: persistent, one block per set: moments level by level,
-//                         deepest first, with a block barrier between levels.
+//   batch_moments_kernel: persistent, one block per set: every leaf in key order,
+//                         then the other cells level by level, deepest first,
+//                         with a block barrier between levels.
 // The paper builds disjoint subtrees on dynamically scheduled threads
 // (Sec. 2.3.3); here the unit of dynamic scheduling is a whole set.
 #include <cfloat>
@@ -415,7 +416,7 @@ __device__ __noinline__ void leaf_sum_f64_serial(const MomOut &o, const float4 *
 
 template <int MODE>
 __global__ void __launch_bounds__(kBMomThreads, 3)
-    batch_moments_kernel(BatchArgs A, TreeIn T, MomOut o) {
+    batch_moments_kernel(BatchArgs A, TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell) {
     if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
     __shared__ int64_t s_lvl[kLevels + 1];
     __shared__ int s_q;
@@ -433,17 +434,19 @@ __global__ void __launch_bounds__(kBMomThreads, 3)
             }
             s_lvl[kLevels] = r;
         }
+        // every leaf of the set first, in key order (neighbouring lanes read
+        // neighbouring records), then the other cells level by level
+        const int64_t l0 = A.set_leaf_off[set], l1 = A.set_leaf_off[set + 1];
+        for (int64_t j = l0 + threadIdx.x; j < l1; j += blockDim.x) {
+            const int64_t c = leaf_cell[j];
+            const int64_t pf = T.pfirst[c], pe = T.pend[c];
+            if (pe - pf > kBigLeafSerial) leaf_sum_f64_serial(o, A.xs, c, pf, pe, MODE == TB_MOM_FP64);
+            else leaf_sum<MODE>(o, A.xs, c, pf, pe);
+        }
         __syncthreads();
-        for (int d = kDepthMax; d >= 0; --d) {
-            for (int64_t c = s_lvl[d] + threadIdx.x; c < s_lvl[d + 1]; c += blockDim.x) {
-                if (T.child_first[c] >= 0) {
-                    combine_children<MODE>(T, o, c);
-                } else {
-                    const int64_t pf = T.pfirst[c], pe = T.pend[c];
-                    if (pe - pf > kBigLeafSerial) leaf_sum_f64_serial(o, A.xs, c, pf, pe, MODE == TB_MOM_FP64);
-                    else leaf_sum<MODE>(o, A.xs, c, pf, pe);
-                }
-            }
+        for (int d = kDepthMax - 1; d >= 0; --d) {
+            for (int64_t c = s_lvl[d] + threadIdx.x; c < s_lvl[d + 1]; c += blockDim.x)
+                if (T.child_first[c] >= 0) combine_children<MODE>(T, o, c);
             __syncthreads();
         }
     }
@@ -520,13 +523,13 @@ cudaError_t launch_batched_t(const BatchArgs &A, int32_t S, int ncrit, tb_tree &
     const int grid_mom = fit(3);
     switch (mode) {
         case TB_MOM_FP32_COMP:
-            batch_moments_kernel<TB_MOM_FP32_COMP><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o);
+            batch_moments_kernel<TB_MOM_FP32_COMP><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o, t.leaf_cell);
             break;
         case TB_MOM_FP32_PLAIN:
-            batch_moments_kernel<TB_MOM_FP32_PLAIN><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o);
+            batch_moments_kernel<TB_MOM_FP32_PLAIN><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o, t.leaf_cell);
             break;
         default:
-            batch_moments_kernel<TB_MOM_FP64><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o);
+            batch_moments_kernel<TB_MOM_FP64><<<grid_mom, kBMomThreads, 0, s>>>(A, Tr, o, t.leaf_cell);
             break;
     }
     ++g_launches;

@@ -305,8 +305,7 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __shared__ uint32_t s_entry[kEfTile];               // k - s | m << 11 | L << 16 | Lprev << 21
     __shared__ uint32_t s_mask[kEfChunks][kLevels];     // level masks of each chunk of 32 starts
     __shared__ uint32_t s_cpre[kEfChunks][kLevels];     // starts of each level in earlier chunks
-    __shared__ uint32_t s_imask[kEfChunks][kLevels];    // the same for non-leaf cells (d < L)
-    __shared__ uint32_t s_ipre[kEfChunks][kLevels];
+    __shared__ uint32_t s_ipre[kEfChunks][kLevels];     // non-leaf cells of each level in earlier chunks
     __shared__ uint32_t s_ibase[kLevels];               // the block's first slot in each level's list
     __shared__ uint32_t s_base[kLevelFields];           // first level-d cell (leaf) of the block
     __shared__ uint32_t s_wcnt[kEfWarps];
@@ -375,10 +374,17 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __syncthreads();
     const int total = (int)s_total;
     const int nchunks = (total + 31) / 32;
-    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose): of
-    // the cells each start opens (levels m..L), and of the non-leaf ones
-    // among them (levels m..L-1)
-    auto transpose = [&](uint32_t v) {
+    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose).  A
+    // start opens a non-leaf cell at level d iff it opens cells at d and at
+    // d + 1 (m <= d < L), so the non-leaf masks are s_mask[d] & s_mask[d + 1].
+    for (int c = warp; c < nchunks; c += kEfWarps) {
+        const int i = c * 32 + lane;
+        uint32_t v = 0;
+        if (i < total) {
+            const uint32_t en = s_entry[i];
+            const uint32_t mm = (en >> 11) & 31u, LL = (en >> 16) & 31u;
+            v = (2u << LL) - (1u << mm);
+        }
         uint32_t msk = 0x0000ffffu;
 #pragma unroll
         for (int j = 16; j > 0; j >>= 1, msk ^= msk << j) {
@@ -386,32 +392,19 @@ __global__ void __launch_bounds__(kEfThreads, 2)
             if (lane & j) v ^= ((y >> j) ^ v) & msk;
             else v ^= (((v >> j) ^ y) & msk) << j;
         }
-        return v;
-    };
-    for (int c = warp; c < nchunks; c += kEfWarps) {
-        const int i = c * 32 + lane;
-        uint32_t v = 0, vi = 0;
-        if (i < total) {
-            const uint32_t en = s_entry[i];
-            const uint32_t mm = (en >> 11) & 31u, LL = (en >> 16) & 31u;
-            v = (2u << LL) - (1u << mm);
-            vi = (1u << LL) - (1u << mm);
-        }
-        v = transpose(v);
-        vi = transpose(vi);
-        if (lane < kLevels) {
-            s_mask[c][lane] = v;
-            s_imask[c][lane] = vi;
-        }
+        if (lane < kLevels) s_mask[c][lane] = v;
     }
     __syncthreads();
+    auto imask = [&](int c, int d) {
+        return d + 1 < kLevels ? s_mask[c][d] & s_mask[c][d + 1] : 0u;
+    };
     if (threadIdx.x < kLevels) {
         uint32_t r = 0, ri = 0;
         for (int c = 0; c < nchunks; ++c) {
             s_cpre[c][threadIdx.x] = r;
             r += __popc(s_mask[c][threadIdx.x]);
             s_ipre[c][threadIdx.x] = ri;
-            ri += __popc(s_imask[c][threadIdx.x]);
+            ri += __popc(imask(c, threadIdx.x));
         }
         // the block's slots in the level's list of non-leaf cells (their
         // order in the list is immaterial: each is combined on its own)
@@ -444,7 +437,7 @@ __global__ void __launch_bounds__(kEfThreads, 2)
             out.child_first[idx] = (d < LL) ? (int32_t)P(d + 1) : -1;
             if (d < LL)
                 out.int_list[info->level_offset[d] + s_ibase[d] + s_ipre[c][d] +
-                             (uint32_t)__popc(s_imask[c][d] & lt)] = (int32_t)idx;
+                             (uint32_t)__popc(imask(c, d) & lt)] = (int32_t)idx;
         }
         out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)P(LL);
     }
