@@ -39,6 +39,69 @@ namespace {
 
 // ------------------------------------------------------------ kernels
 
+// Shuffle every field of an accumulator down the warp by `off` lanes.
+template <class Acc>
+__device__ __forceinline__ Acc shfl_down_acc(const Acc &a, int off) {
+    Acc b;
+    constexpr int W = sizeof(Acc) / 4;
+    static_assert(sizeof(Acc) % 4 == 0, "accumulators are made of 4-byte words");
+    const uint32_t *u = reinterpret_cast<const uint32_t *>(&a);
+    uint32_t *v = reinterpret_cast<uint32_t *>(&b);
+#pragma unroll
+    for (int i = 0; i < W; ++i) v[i] = __shfl_down_sync(0xffffffffu, u[i], off);
+    return b;
+}
+
+// One leaf [pf, pe) summed by a whole warp (all 32 lanes call it): each lane
+// sums a stride of the members about the leaf's first member, then the
+// lanes' sums merge in a fixed tree (compensated merges in the compensated
+// mode) and lane 0 writes the cell.  `src` is any source of key-ordered
+// records (shared memory, or a PermSrc).
+template <int MODE, class Src>
+__device__ __forceinline__ void warp_leaf_sum(const MomOut &o, Src src, int64_t c, int64_t pf,
+                                              int64_t pe) {
+    using Acc = typename std::conditional<
+        MODE == TB_MOM_FP64, AccD,
+        typename std::conditional<MODE == TB_MOM_FP32_COMP, AccC, AccP>::type>::type;
+    const int lane = threadIdx.x & 31;
+    const float4 r0 = src[pf];
+    const float ref[3] = {r0.x, r0.y, r0.z};
+    float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
+    Acc A;
+    A.init();
+    for (int64_t k = pf + lane; k < pe; k += 32) {
+        const float4 v = src[k];
+        const float x[3] = {v.x, v.y, v.z};
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(bb[a], x[a]);
+            bb[3 + a] = fmaxf(bb[3 + a], x[a]);
+        }
+        if constexpr (MODE == TB_MOM_FP64) {
+            const double dx[3] = {(double)x[0] - (double)ref[0], (double)x[1] - (double)ref[1],
+                                  (double)x[2] - (double)ref[2]};
+            A.add((double)v.w, dx);
+        } else {
+            const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
+                                 __fsub_rn(x[2], ref[2])};
+            A.add(v.w, dx);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Acc B = shfl_down_acc(A, off);
+        A.merge(B);
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(bb[a], __shfl_down_sync(0xffffffffu, bb[a], off));
+            bb[3 + a] = fmaxf(bb[3 + a], __shfl_down_sync(0xffffffffu, bb[3 + a], off));
+        }
+    }
+    if (lane == 0) {
+        if constexpr (MODE == TB_MOM_FP64) finish_d(o, c, A, ref, bb, true);
+        else if constexpr (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
+        else finish_p(o, c, A, ref, bb);
+    }
+}
+
 // Leaves, one block per tile of kLtTile consecutive key-order positions.
 //   1. The permutation of the tile and of a halo of kLtHalo positions past
 //      it is bulk-copied (TMA) into shared memory, and m_k | L_k << 8 of the
@@ -71,6 +134,11 @@ struct LeafTileSmem {
     uint16_t start[kLtTile];                   // offsets of the leaf starts in the tile
     uint32_t wcount[kLtThreads / 32];
     int32_t next_start;                        // first start at or past the tile end, or -1
+    // compensated mode: staged leaves of more than kSplitLeaf members, summed
+    // by whole warps after the short ones (at most kLtTile / 17 of them)
+    int32_t long_c[kLtTile / (kSplitLeaf + 1) + 1];
+    uint32_t long_x[kLtTile / (kSplitLeaf + 1) + 1];   // start | end << 16 (tile offsets)
+    uint32_t n_long;
     uint64_t bar;
 };
 
@@ -189,7 +257,10 @@ __global__ void __launch_bounds__(kLtThreads, 4)
         }
         // the end of the array ends the last leaf
         if (nx < 0 && k0 + span == n) nx = span;
-        if (lane == 0) S.next_start = nx;
+        if (lane == 0) {
+            S.next_start = nx;
+            S.n_long = 0;
+        }
     }
     __syncthreads();
     uint32_t before = 0, total = 0;
@@ -216,41 +287,34 @@ __global__ void __launch_bounds__(kLtThreads, 4)
             continue;
         }
         if (MODE == TB_MOM_FP32_COMP && xe - x > kSplitLeaf) {
-            long_queue[atomicAdd(&info->misc_ctr[5], 1u)] = (int32_t)c;
+            const uint32_t q = atomicAdd(&S.n_long, 1u);
+            S.long_c[q] = (int32_t)c;
+            S.long_x[q] = (uint32_t)x | ((uint32_t)xe << 16);
             continue;
         }
         if constexpr (MODE == TB_MOM_FP32_COMP) leaf_sum_split(o, (const float4 *)S.rec, c, x, xe);
         else leaf_sum<MODE>(o, (const float4 *)S.rec, c, x, xe);
     }
+    if constexpr (MODE == TB_MOM_FP32_COMP) {
+        __syncthreads();
+        const uint32_t nl = S.n_long;
+        for (uint32_t q = warp; q < nl; q += kLtThreads / 32) {
+            const uint32_t xx = S.long_x[q];
+            warp_leaf_sum<TB_MOM_FP32_COMP>(o, (const float4 *)S.rec, S.long_c[q], xx & 0xffffu,
+                                            xx >> 16);
+        }
+    }
     if (xs && threadIdx.x == 0) bulk_store_wait_read();
 }
 
-// Shuffle every field of an accumulator down the warp by `off` lanes.
-template <class Acc>
-__device__ __forceinline__ Acc shfl_down_acc(const Acc &a, int off) {
-    Acc b;
-    constexpr int W = sizeof(Acc) / 4;
-    static_assert(sizeof(Acc) % 4 == 0, "accumulators are made of 4-byte words");
-    const uint32_t *u = reinterpret_cast<const uint32_t *>(&a);
-    uint32_t *v = reinterpret_cast<uint32_t *>(&b);
-#pragma unroll
-    for (int i = 0; i < W; ++i) v[i] = __shfl_down_sync(0xffffffffu, u[i], off);
-    return b;
-}
-
 // The queued leaves, one warp per leaf, members read through the
-// permutation (32 independent loads per round): each lane sums a stride of
-// the members about the leaf's first member, then the lanes' sums merge in a
-// fixed tree (compensated merges in the compensated mode).  Leaves of more
-// than kBigLeafThread members -- only depth-21 leaves of identical keys --
-// are queued again for big_leaf_kernel.
+// permutation (32 independent loads per round).  Leaves of more than
+// kBigLeafThread members -- only depth-21 leaves of identical keys -- are
+// queued again for big_leaf_kernel.
 template <int MODE>
 __global__ void __launch_bounds__(kMomThreads, 4)
     long_leaf_kernel(TreeIn T, MomOut o, PermSrc src, const int32_t *long_queue, DevInfo *info) {
     if (info->status & (kErrOverflow | kErrNonFinite | kErrTimeout)) return;
-    using Acc = typename std::conditional<
-        MODE == TB_MOM_FP64, AccD,
-        typename std::conditional<MODE == TB_MOM_FP32_COMP, AccC, AccP>::type>::type;
     const int lane = threadIdx.x & 31;
     const int64_t nq = *(volatile const uint32_t *)&info->misc_ctr[5];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
@@ -261,42 +325,7 @@ __global__ void __launch_bounds__(kMomThreads, 4)
             if (lane == 0) T.big_leaf[atomicAdd(&info->misc_ctr[2], 1u)] = (int32_t)c;
             continue;
         }
-        const float4 r0 = src[pf];
-        const float ref[3] = {r0.x, r0.y, r0.z};
-        float bb[6] = {r0.x, r0.y, r0.z, r0.x, r0.y, r0.z};
-        Acc A;
-        A.init();
-        for (int64_t k = pf + lane; k < pe; k += 32) {
-            const float4 v = src[k];
-            const float x[3] = {v.x, v.y, v.z};
-            for (int a = 0; a < 3; ++a) {
-                bb[a] = fminf(bb[a], x[a]);
-                bb[3 + a] = fmaxf(bb[3 + a], x[a]);
-            }
-            if constexpr (MODE == TB_MOM_FP64) {
-                const double dx[3] = {(double)x[0] - (double)ref[0], (double)x[1] - (double)ref[1],
-                                      (double)x[2] - (double)ref[2]};
-                A.add((double)v.w, dx);
-            } else {
-                const float dx[3] = {__fsub_rn(x[0], ref[0]), __fsub_rn(x[1], ref[1]),
-                                     __fsub_rn(x[2], ref[2])};
-                A.add(v.w, dx);
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const Acc B = shfl_down_acc(A, off);
-            A.merge(B);
-            for (int a = 0; a < 3; ++a) {
-                bb[a] = fminf(bb[a], __shfl_down_sync(0xffffffffu, bb[a], off));
-                bb[3 + a] = fmaxf(bb[3 + a], __shfl_down_sync(0xffffffffu, bb[3 + a], off));
-            }
-        }
-        if (lane == 0) {
-            if constexpr (MODE == TB_MOM_FP64) finish_d(o, c, A, ref, bb, true);
-            else if constexpr (MODE == TB_MOM_FP32_COMP) finish_c(o, c, A, ref, bb);
-            else finish_p(o, c, A, ref, bb);
-        }
+        warp_leaf_sum<MODE>(o, src, c, pf, pe);
     }
 }
 
