@@ -457,22 +457,31 @@ def run_ours(a):
             cev[t_][1].record(cstream)
             copied[b_].record(cstream)
 
+        tree.profile(True)
+        tree.stage_times()
         copy_in(0, 0)
         for t_ in range(a.steps):
             b_ = t_ % 2
             stream.wait_event(copied[b_])
             pb, wb = bufs[b_]
             tb.build(pb, wb, n_crit=n_crit, cell_capacity=C, sort_cfg=cfg, tree=tree, key_order=ko)
+            # the build reads the inputs only for the root cell and the keys;
+            # the moments sum the snapshot the key pass took, so the buffer
+            # is free for the next copy once the build's work is done
+            used[b_].record(stream)
             tb.moments(tree, pb, wb)
             root = torch.cat([tree.mass[:1], tree.com[0], tree.quad[0]])
             res.copy_(root, non_blocking=True)
-            used[b_].record(stream)
             if t_ + 1 < a.steps:
                 if t_ >= 1:
-                    cstream.wait_event(used[1 - b_])   # step t - 1 is done with that buffer
+                    cstream.wait_event(used[1 - b_])   # step t - 1's build is done with it
                 copy_in(1 - b_, t_ + 1)
         f1.record(stream)
         torch.cuda.synchronize()
+        e_stages = {}
+        for name_, v_ in tree.stage_times():
+            e_stages[name_] = e_stages.get(name_, 0.0) + v_ / a.steps
+        tree.profile(False)
         ems = f0.elapsed_time(f1)
         ems, evalue = whole_job_rate(n, a.steps, world, ems)
         copy_ms = [c0.elapsed_time(c1) for c0, c1 in cev]
@@ -485,7 +494,8 @@ def run_ours(a):
                       "h2d_gbs_median": round(h2d_bytes / (float(np.median(copy_ms)) / 1e3) / 1e9, 1),
                       "pipelining": "step t+1's H2D copy overlaps step t's build (two input "
                                     "buffers); copy times from events around each in-loop copy "
-                                    "on the copy stream"}
+                                    "on the copy stream",
+                      "stage_ms": {k: round(v, 4) for k, v in e_stages.items()}}
         del p2, w2
 
     # key-ordered input: what a simulation sees when it reorders its particle

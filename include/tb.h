@@ -176,8 +176,11 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
  * the centre of mass of a parent from those of its children; higher
  * multipoles likewise).  tb_build keeps a snapshot of (x, y, z, m) taken
  * while it made the keys; when d_pos and d_mass are the same pointers the
- * build was given, that snapshot is used, so their contents must not change
- * in between.  Other pointers are read afresh.  Cells of more than 2^20
+ * build was given, that snapshot is used and the arrays are not read again
+ * (new contents written in between are not seen: the moments are those of
+ * the particles the tree was built from).  So once the build's work on the
+ * stream has completed, the caller may refill those arrays, e.g. with the
+ * next step's copy.  Other pointers are read afresh.  Cells of more than 2^20
  * particles are summed in FP64 in every mode.  Returns TB_EINVAL when the
  * tree's last tb_build returned an error before it enqueued every stage. */
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
