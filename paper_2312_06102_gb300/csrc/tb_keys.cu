@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
 }
 
 template <int RADIX_BITS, bool HILBERT>
-__global__ void __launch_bounds__(kKeysThreads) keys_kernel(const float *__restrict__ pos,
+__global__ void __launch_bounds__(kKeysThreads, 6) keys_kernel(const float *__restrict__ pos,
                                                             const float *__restrict__ mass,
                                                             float m_eq, int64_t n, bool vec,
                                                             uint64_t *__restrict__ keys,
@@ -304,7 +304,8 @@ static cudaError_t keys_impl(const float *pos, const float *mass, int64_t n, uin
     if (first_on_device(attr_done)) {
         cudaFuncSetAttribute(keys_kernel<B, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     }
-    int64_t grid = 152 * 4;
+    // six resident blocks per SM (42 registers), one wave
+    int64_t grid = 152 * 6;
     int64_t need = (n + 4 * kKeysThreads - 1) / (4 * kKeysThreads);
     if (need < grid) grid = need < 1 ? 1 : need;
     keys_kernel<B, H><<<(unsigned)grid, kKeysThreads, smem, s>>>(pos, mass, m_eq, n, vec, keys, ws.xm,
