@@ -632,10 +632,29 @@ def run_walk(a, tb, torch):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     ok = t.sync() == 0 and bool(torch.isfinite(acc).all())
+    # one more walk, untimed, with profiling on: it counts its interactions
+    t.profile(True)
+    tb.walk(t, 0.75, eps, n_group=128, out=acc)
+    cells, pairs = tb.walk_counts(t)
+    t.profile(False)
     t.free()
+    # FP32 operations per interaction as the walk evaluates them (an FMA is 2,
+    # rsqrt / sqrt / reciprocal 1): a particle pair 19 (offset 3, softened
+    # point mass 16), a cell with its quadrupole 66 (double-float offset 6,
+    # point mass 16, quadrupole term 44).  Peak: 152 SMs x 128 FP32 lanes x
+    # 2 x 2.07 GHz = 80.5 TFLOP/s.
+    flops = 19 * pairs + 66 * cells
+    peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12
+    tf = flops / (ms / 1e3) / 1e12
     return {"workload": "plummer n=2^22 (seed 7)", "theta": 0.75, "n_crit": 10, "n_group": 128,
             "quadrupole": True, "ms": round(ms, 3), "mparticles_s": round(n / (ms / 1e3) / 1e6, 2),
-            "finite": ok}
+            "finite": ok,
+            "interactions": {"cell": cells, "particle": pairs,
+                             "per_particle": round((cells + pairs) / n, 1),
+                             "g_per_s": round((cells + pairs) / (ms / 1e3) / 1e9, 1)},
+            "roofline": {"bound": "alu", "achieved": round(tf, 2), "peak": round(peak_tf, 1),
+                         "unit": "TFLOP/s", "frac": round(tf / peak_tf, 4),
+                         "flops_per_interaction": {"particle": 19, "cell_quadrupole": 66}}}
 
 
 def run_batched(a, tb, torch):

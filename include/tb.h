@@ -231,6 +231,16 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
 tb_status tb_walk(tb_tree *tree, float theta, float eps, int32_t n_group, int32_t use_quad,
                   float *d_acc, tb_stream stream);
 
+/* Interactions evaluated by the last tb_walk of `tree` made while profiling
+ * was enabled on it (tb_profile; counting costs such a walk about 15%):
+ * target particle x accepted cell, and target particle x source particle
+ * (self pairs excluded).  With theta = 0 no cell is accepted and the second
+ * count is n (n - 1).  Both are 0 before the first walk; after a walk made
+ * without profiling they are 0 too.  Synchronises `stream`.
+ * Returns TB_OK, TB_EINVAL (NULL argument) or TB_ECUDA. */
+tb_status tb_walk_counts(tb_tree *tree, tb_stream stream, int64_t *cell_interactions,
+                         int64_t *particle_interactions);
+
 /* Reorder a per-particle array into the key order of a built single tree
  * (Sec. 2.3 step 3; done "every few steps" in a simulation so that later
  * builds start from nearly sorted particles):
@@ -268,7 +278,8 @@ int32_t tb_sort_variant(int32_t i, int32_t *radix_bits, int32_t *threads, int32_
 int64_t tb_kernel_launches(void);
 
 /* Per-stage timing of the most recent builds of `tree`.  When enabled the
- * library records CUDA events on the build stream at each stage boundary.
+ * library records CUDA events on the build stream at each stage boundary,
+ * and tb_walk counts its interactions (tb_walk_counts).
  * tb_stage_times synchronises the stream and writes up to `max` elapsed
  * times (ms) of the last build and moment call, returning the count; names
  * come from tb_stage_name.  Stage 0 is the root cell, 1 the keys, 2..1+P the

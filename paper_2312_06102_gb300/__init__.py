@@ -29,6 +29,7 @@ from ._lib import (  # noqa: F401
     keys_sorted_noalloc,
     reorder,
     walk,
+    walk_counts,
     lib,
     library_path,
     moments,

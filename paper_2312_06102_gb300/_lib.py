@@ -94,6 +94,8 @@ def lib():
         L.tb_reorder.restype = C.c_int
         L.tb_selftest_wait.argtypes = [C.c_int64, _vp]
         L.tb_selftest_wait.restype = C.c_int
+        L.tb_walk_counts.argtypes = [P(TreeC), _vp, P(C.c_int64), P(C.c_int64)]
+        L.tb_walk_counts.restype = C.c_int
         L.tb_set_wait_limit.argtypes = [C.c_int64]
         L.tb_set_wait_limit.restype = C.c_int
         _lib = L
@@ -348,3 +350,12 @@ def set_wait_limit(polls: int) -> int:
     """tb_set_wait_limit: polls after which a radix-pass look-back wait gives
     up (0 restores the default)."""
     return int(lib().tb_set_wait_limit(int(polls)))
+
+
+def walk_counts(tree: Tree, stream=None):
+    """tb_walk_counts: (target-cell, target-particle) interactions of the
+    tree's last walk."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().tb_walk_counts(tree._p, _stream(stream), C.byref(a), C.byref(b)),
+           "tb_walk_counts")
+    return int(a.value), int(b.value)

@@ -558,6 +558,22 @@ const char *tb_stage_name(tb_tree *tree, int32_t i) {
     return ws.ev_name[i + 1];
 }
 
+tb_status tb_walk_counts(tb_tree *tree, tb_stream stream, int64_t *cell_interactions,
+                         int64_t *particle_interactions) {
+    if (!tree || !cell_interactions || !particle_interactions) return TB_EINVAL;
+    Workspace &ws = state_of(tree)->ws;
+    *cell_interactions = *particle_interactions = 0;
+    if (!ws.walk_ctr) return TB_OK;
+    unsigned long long h[2] = {0, 0};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h, ws.walk_ctr + 2, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    *cell_interactions = (int64_t)h[0];
+    *particle_interactions = (int64_t)h[1];
+    return TB_OK;
+}
+
 tb_status tb_set_wait_limit(int64_t polls) {
     if (polls < 0) return TB_EINVAL;
     g_wait_limit = polls > 0 ? polls : kDefaultWaitLimit;

@@ -113,6 +113,7 @@ struct Workspace {
     // tree walk scratch and whether the moments match the current structure
     int32_t *walk = nullptr;
     int64_t walk_cap = 0;
+    uint32_t *walk_ctr = nullptr;   // counters of the last walk (groups, tickets, interactions)
     bool moments_ready = false;
     bool xs_current = false;      // xs holds the records of the last moments in key order
     bool cells_ready = false;     // the last tb_build enqueued every stage

@@ -26,7 +26,9 @@
 // with Q the cell's central second moment and r = x - COM (unsoftened).
 // Offsets are taken as (x - com) - com_lo, exact to one rounding when the
 // target and the centre are close.  The result is written in the caller's
-// particle order.
+// particle order.  A walk on a tree with profiling enabled also counts the
+// interactions it evaluated (target-cell and target-particle pairs), read
+// back by tb_walk_counts.
 #include "tb_device.cuh"
 
 namespace tb {
@@ -135,6 +137,7 @@ __global__ void walk_groups_kernel(const int32_t *__restrict__ parent, const int
     }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(kWalkThreads)
     walk_kernel(WalkTree T, const int32_t *__restrict__ groups, uint32_t *ctr, int32_t *stacks,
                 float theta, float eps2, int use_quad, float *__restrict__ acc_out, DevInfo *info) {
@@ -146,11 +149,33 @@ __global__ void __launch_bounds__(kWalkThreads)
     const uint32_t ngroups = *(volatile const uint32_t *)&ctr[0];
     const unsigned lt = lanemask_lt();
     const float side = (float)T.side;
+    // interactions evaluated by this warp (lane 0 counts): target x accepted
+    // cell, and target x source particle (self excluded); added to the
+    // walk's totals when the warp is done
+    unsigned long long n_cell_int = 0, n_pp_int = 0;
+    unsigned long long *totals = reinterpret_cast<unsigned long long *>(ctr + 2);
+    auto count = [&](int ncell, int nrange, int64_t nt) {
+        if (!COUNT) return;
+        long long srcs = 0;
+        for (int j = lane; j < nrange; j += 32) srcs += W.range[j].y - W.range[j].x;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) srcs += __shfl_xor_sync(0xffffffffu, srcs, off);
+        if (lane == 0) {
+            n_cell_int += (unsigned long long)(ncell * nt);
+            n_pp_int += (unsigned long long)(srcs * nt);
+        }
+    };
     for (;;) {
         uint32_t gi = 0;
         if (lane == 0) gi = atomicAdd(&ctr[1], 1u);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= ngroups) return;
+        if (gi >= ngroups) {
+            if (COUNT && lane == 0) {
+                atomicAdd(&totals[0], n_cell_int);
+                atomicAdd(&totals[1], n_pp_int);
+            }
+            return;
+        }
         const int32_t g = groups[gi];
         const int64_t gpf = T.pfirst[g], gpe = T.pend[g];
         for (int64_t kb = gpf; kb < gpe; kb += 32) {
@@ -178,6 +203,7 @@ __global__ void __launch_bounds__(kWalkThreads)
                 // room for this round: 32 accepted cells or leaf ranges, and
                 // 7 more stack entries per cell taken
                 if (ncell + 32 > kCellCap || nrange + 32 > kRangeCap) {
+                    count(ncell, nrange, ke - kb);
                     acc = evaluate(T, W, ncell, nrange, k, ke, eps2, use_quad != 0, acc);
                     ncell = nrange = 0;
                     __syncwarp();
@@ -235,6 +261,8 @@ __global__ void __launch_bounds__(kWalkThreads)
                 if (lane == 0) atomicOr(&info->status, kErrWalk);
                 return;
             }
+            count(ncell, nrange, ke - kb);
+            if (COUNT && lane == 0) n_pp_int -= (unsigned long long)(ke - kb);   // own pairs
             acc = evaluate(T, W, ncell, nrange, k, ke, eps2, use_quad != 0, acc);
             __syncwarp();
             if (k < ke) {
@@ -257,6 +285,7 @@ cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps,
                         int use_quad, float *acc, int32_t *buf, cudaStream_t s) {
     float4 *rec = reinterpret_cast<float4 *>(buf);   // first: 16-byte aligned
     uint32_t *ctr = reinterpret_cast<uint32_t *>(buf + 16 * t.n_cells);
+    ws.walk_ctr = ctr;
     int32_t *groups = buf + 16 * t.n_cells + 8;
     int32_t *stacks = groups + t.n_cells;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), s);
@@ -273,8 +302,14 @@ cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     WalkTree T{t.child_first, t.child_end, t.pfirst, t.pend, t.level, t.mass, t.com, t.com_lo,
                t.quad, t.aabb, ws.xs, t.perm, t.side, rec};
-    walk_kernel<<<kWalkBlocks, kWalkThreads, 0, s>>>(T, groups, ctr, stacks, theta, eps * eps,
-                                                     use_quad, acc, ws.info);
+    // the interaction counts cost about 15% of the walk: only profiled walks
+    // take them
+    if (ws.profile)
+        walk_kernel<true><<<kWalkBlocks, kWalkThreads, 0, s>>>(T, groups, ctr, stacks, theta,
+                                                               eps * eps, use_quad, acc, ws.info);
+    else
+        walk_kernel<false><<<kWalkBlocks, kWalkThreads, 0, s>>>(T, groups, ctr, stacks, theta,
+                                                                eps * eps, use_quad, acc, ws.info);
     ++g_launches;
     return cudaGetLastError();
 }

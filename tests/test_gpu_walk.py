@@ -44,12 +44,40 @@ def test_theta_zero_is_the_direct_sum(gen):
     pos, mass = plummer(n, 41) if gen == "plummer" else exponential_disk(n, 41)
     m, t = _setup(pos, mass)
     eps = 1e-3 * t.side
+    t.profile(True)                 # the walk counts its interactions
     acc = to_np(m.walk(t, 0.0, eps, n_group=32)).astype(np.float64)
+    t.profile(False)
     tg = _targets(n, 300, 1)
     ref = oracle.direct_acc(pos, mass, tg, eps)
     e = _rel(acc[tg], ref)
     # FP32 sums of 12,000 terms: a few sqrt(N) u in the median
     assert np.median(e) <= 1e-5 and e.max() <= 1e-3, (np.median(e), e.max())
+    # no cell is accepted at theta 0: every pair once, self pairs excluded
+    assert m.walk_counts(t) == (0, n * (n - 1))
+
+
+def test_interaction_counts_at_half():
+    """At theta 0.5 cells stand in for most particles: far fewer than n (n - 1)
+    pair evaluations, and every target still sees n - 1 sources' worth of mass
+    (checked through the accelerations elsewhere); the counts are stable
+    across repeated walks."""
+    n = 20_000
+    pos, mass = plummer(n, 43)
+    m, t = _setup(pos, mass)
+    eps = 1e-3 * t.side
+    t.profile(True)
+    a1 = to_np(m.walk(t, 0.5, eps, n_group=64))
+    c1 = m.walk_counts(t)
+    m.walk(t, 0.5, eps, n_group=64)
+    assert m.walk_counts(t) == c1
+    cells, pairs = c1
+    assert cells > 0 and 0 < pairs < n * (n - 1) // 4
+    # the counting walk gives the same accelerations as the plain one, and a
+    # walk made without profiling counts nothing
+    t.profile(False)
+    a2 = to_np(m.walk(t, 0.5, eps, n_group=64))
+    assert np.array_equal(a1, a2)
+    assert m.walk_counts(t) == (0, 0)
 
 
 @pytest.mark.parametrize("n_group", [1, 32, 64, 200])
