@@ -711,6 +711,27 @@ def run_batched(a, tb, torch):
         raise RuntimeError(f"batched replay failed: {tb.STATUS[st]}")
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     batched_ms = float(np.median(ms))
+    # the same build as one cooperative launch (tb_params.batch_one_launch),
+    # captured and replayed the same way, for the record
+    g_one = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream,
+                         batch_threads=bt, one_launch=True)
+        stream.synchronize()
+        with torch.cuda.graph(g_one, stream=stream):
+            tb.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, tree=tree, stream=stream,
+                             batch_threads=bt, one_launch=True)
+        for _ in range(3):
+            g_one.replay()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(20):
+            g_one.replay()
+        o1.record(stream)
+        stream.synchronize()
+    one_ms = o0.elapsed_time(o1) / 20
+    if tree.sync(stream) != 0:
+        raise RuntimeError("one-launch batched replay failed")
     # stage times of a few builds outside the graph (events at stage ends)
     tree.profile(True)
     tree.stage_times(stream)
@@ -760,6 +781,7 @@ def run_batched(a, tb, torch):
             "speedup_vs_plain": round(plain_ms / batched_ms, 1),
             "kernels_per_batched_build": int(per_build),
             "batch_threads": int(bt) if bt else 512,
+            "one_launch_ms_per_build": round(one_ms, 4),
             "batch_threads_autotune_ms": ({str(k): round(v, 3) for k, v in bt_ms.items()}
                                           if bt_ms else None),
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},

@@ -104,6 +104,10 @@ typedef struct {
                                 for 0) or 1024 (one) */
     int32_t key_order;       /* tb_key_order: TB_KEYS_MORTON (default) or TB_KEYS_HILBERT
                                 (tb_build only; tb_build_batched takes Morton keys) */
+    int32_t batch_one_launch; /* tb_build_batched with cell_capacity > 0 only: 1 runs the
+                                whole build as one cooperative launch (phases separated
+                                by grid barriers); 0 (default) runs it as separate
+                                launches, which measured faster */
 } tb_params;
 
 /* Host-side description of a tree.  Scalars are valid after a build with
@@ -194,7 +198,10 @@ tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_
  * Every set must hold at most 2^31 - 1 particles.  With
  * params.cell_capacity > 0 and a tree from an earlier call with the same S
  * and n_total, nothing is allocated and nothing synchronises, so the call can
- * be captured into a CUDA graph and replayed.
+ * be captured into a CUDA graph and replayed.  With batch_one_launch set the
+ * whole build is then one cooperative launch (persistent blocks taking sets
+ * from work queues, phases separated by grid barriers with bounded waits);
+ * otherwise, and always with cell_capacity 0, it takes separate launches.
  * Of params it reads n_crit, mom_mode, cell_capacity and batch_threads;
  * key_order must be TB_KEYS_MORTON.  Each set is sorted by one block (five
  * 8-bit passes over the upper 40 key bits, then its runs of equal upper

@@ -26,7 +26,8 @@ class TbError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("n_crit", C.c_int32), ("mom_mode", C.c_int32), ("cell_capacity", C.c_int64),
                 ("reorder", C.c_int32), ("radix_bits", C.c_int32), ("sort_threads", C.c_int32),
-                ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("key_order", C.c_int32)]
+                ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("key_order", C.c_int32),
+                ("batch_one_launch", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -282,8 +283,10 @@ def moments(tree: Tree, pos: torch.Tensor, mass: torch.Tensor | None = None, str
 def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: torch.Tensor,
                   n_crit: int = 16, mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0,
                   radix_bits: int = 0, batch_threads: int = 0, tree: Tree | None = None,
-                  n_total: int | None = None, stream=None, key_order: int = KEYS_MORTON) -> Tree:
-    """tb_build_batched: set s holds pos[set_offsets[s]:set_offsets[s+1]]."""
+                  n_total: int | None = None, stream=None, key_order: int = KEYS_MORTON,
+                  one_launch: bool = False) -> Tree:
+    """tb_build_batched: set s holds pos[set_offsets[s]:set_offsets[s+1]];
+    one_launch (with cell_capacity > 0) runs it as one cooperative launch."""
     if set_offsets.dtype != torch.int64 or not set_offsets.is_cuda:
         raise ValueError("set_offsets must be an int64 CUDA tensor")
     t = tree if tree is not None else Tree()
@@ -293,6 +296,7 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
                                                 pos.shape[0] if n_total is None else n_total) or 0
     p = _params(n_crit, mom_mode, cell_capacity, 0, radix_bits, batch_threads)
     p.key_order = int(key_order)
+    p.batch_one_launch = int(bool(one_launch))
     n_total = pos.shape[0] if n_total is None else n_total
     code = lib().tb_build_batched(_ptr(pos), _ptr(mass), _ptr(set_offsets),
                                   set_offsets.shape[0] - 1, int(n_total), C.byref(p),

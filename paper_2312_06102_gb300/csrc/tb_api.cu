@@ -212,6 +212,7 @@ bool valid_params(const tb_params *p) {
            (p->radix_bits == 0 || (p->radix_bits >= 8 && p->radix_bits <= 11)) &&
            (p->key_order == TB_KEYS_MORTON || p->key_order == TB_KEYS_HILBERT) &&
            batch_threads_valid(p->batch_threads) &&
+           (p->batch_one_launch == 0 || p->batch_one_launch == 1) &&
            sort_cfg_valid(pick_cfg(p));
 }
 
@@ -452,7 +453,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
         dev_free(t.set_particle_offset); dev_free(t.set_cell_offset); dev_free(t.set_root);
         const int64_t cap = n_sets > 0 ? n_sets : 1;
         if (!dev_alloc(ws.set_order, cap) || !dev_alloc(ws.set_cnt, cap * kLevelFields) ||
-            !dev_alloc(ws.set_leaf_off, cap + 1) || !dev_alloc(ws.set_ctr, 4) ||
+            !dev_alloc(ws.set_leaf_off, cap + 1) || !dev_alloc(ws.set_ctr, 8) ||
             !dev_alloc(t.set_particle_offset, cap + 1) || !dev_alloc(t.set_cell_offset, cap + 1) ||
             !dev_alloc(t.set_root, 4 * cap))
             return TB_ENOMEM;
@@ -463,7 +464,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
         if (st != TB_OK) return st;
     }
     cudaError_t e = cudaMemsetAsync(ws.info, 0, sizeof(DevInfo), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws.set_ctr, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.set_ctr, 0, 8 * sizeof(uint32_t), s);
     if (e == cudaSuccess && n_sets > 0)
         e = cudaMemcpyAsync(t.set_particle_offset, d_set_offsets, sizeof(int64_t) * (n_sets + 1),
                             cudaMemcpyDeviceToDevice, s);
@@ -480,6 +481,15 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
         return TB_OK;
     }
     mark(ws, "start", s);
+    if (params->cell_capacity > 0 && params->batch_one_launch) {
+        // fixed capacity: the whole build in one cooperative launch
+        e = launch_batched_one(d_pos, d_mass, t.set_particle_offset, n_sets, n_total,
+                               params->n_crit, params->batch_threads, t, ws, params->cell_capacity,
+                               params->mom_mode, s);
+        if (e == cudaSuccess) return TB_OK;
+        // a device that cannot take it: the same build in separate launches
+        cudaGetLastError();
+    }
     e = launch_set_check(t.set_particle_offset, n_sets, n_total, ws, s);
     if (e == cudaSuccess)
         e = launch_batched(d_pos, d_mass, t.set_particle_offset, n_sets, params->n_crit,

@@ -63,7 +63,7 @@ struct BatchArgs {
     int64_t *set_cell_off;    // [S+1]
     int64_t *set_leaf_off;    // [S+1]
     double *set_root;         // [S][4]
-    uint32_t *queue;          // [4] work-queue tickets
+    uint32_t *queue;          // [8] work-queue tickets [0..2], grid barrier [4..5]
     DevInfo *info;
 };
 
@@ -75,9 +75,8 @@ __host__ __device__ inline size_t batch_front_smem(int ncrit) {
 
 // Sets in descending size classes (floor(log2 size)), ascending index within
 // a class: the largest sets are taken from the queues first.
-__global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int32_t S,
-                                                         int32_t *order, const DevInfo *info) {
-    if (info->status & kErrInvalid) return;
+// One block of up to 1024 threads (a multiple of 32).
+__device__ void set_order_block(const int64_t *off, int32_t S, int32_t *order) {
     __shared__ uint32_t cls[34];
     if (threadIdx.x < 34) cls[threadIdx.x] = 0;
     __syncthreads();
@@ -99,7 +98,8 @@ __global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int
     __shared__ uint32_t tot[34];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < S; c0 += 1024) {
+    const int nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 < S; c0 += blockDim.x) {
         for (int i = threadIdx.x; i < 32 * 34; i += blockDim.x) (&wc[0][0])[i] = 0;
         __syncthreads();
         const int s = c0 + (int)threadIdx.x;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int
         __syncthreads();
         if (threadIdx.x < 34) {
             uint32_t r = 0;
-            for (int w = 0; w < 32; ++w) { const uint32_t v = wc[w][threadIdx.x]; wc[w][threadIdx.x] = r; r += v; }
+            for (int w = 0; w < nw; ++w) { const uint32_t v = wc[w][threadIdx.x]; wc[w][threadIdx.x] = r; r += v; }
             tot[threadIdx.x] = r;
         }
         __syncthreads();
@@ -118,6 +118,12 @@ __global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int
         if (threadIdx.x < 34) cls[threadIdx.x] += tot[threadIdx.x];
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(1024) set_order_kernel(const int64_t *off, int32_t S,
+                                                         int32_t *order, const DevInfo *info) {
+    if (info->status & kErrInvalid) return;
+    set_order_block(off, S, order);
 }
 
 __device__ __forceinline__ int take_set(uint32_t *ticket, int32_t S, int *s_q) {
@@ -163,10 +169,10 @@ __device__ void set_root_cube(const float *__restrict__ pos, int64_t o, int64_t 
     __syncthreads();
 }
 
+// Every set from work queue 0: root cube, keys, sort, counts.  `raw` is the
+// block's dynamic shared memory (batch_front_smem<T> bytes).
 template <int T>
-__global__ void __launch_bounds__(T, 1024 / T) batch_front_kernel(BatchArgs A) {
-    if (A.info->status & kErrInvalid) return;
-    extern __shared__ __align__(16) unsigned char raw[];
+__device__ void front_sets(const BatchArgs &A, unsigned char *raw) {
     CtaSortSharedT<T> &sm = *reinterpret_cast<CtaSortSharedT<T> *>(raw);
     __shared__ TileSharedT<T> ts;
     __shared__ float s_red[(T / 32) * 6];
@@ -288,13 +294,21 @@ __global__ void __launch_bounds__(T, 1024 / T) batch_front_kernel(BatchArgs A) {
     }
 }
 
-// Cell and leaf offsets of the sets (in set order), totals and depth.
-__global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t cell_cap) {
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) batch_front_kernel(BatchArgs A) {
     if (A.info->status & kErrInvalid) return;
+    extern __shared__ __align__(16) unsigned char raw[];
+    front_sets<T>(A, raw);
+}
+
+// Cell and leaf offsets of the sets (in set order), totals and depth.
+// One block of up to 1024 threads.
+__device__ void batch_scan_block(const BatchArgs &A, int64_t cell_cap) {
     __shared__ int64_t s_c[1024], s_l[1024];
     __shared__ int s_dmax;
     const int S = A.n_sets;
-    const int per = (S + 1023) / 1024;
+    const int nt = blockDim.x;
+    const int per = (S + nt - 1) / nt;
     const int lo = threadIdx.x * per, hi = min(S, lo + per);
     int64_t c = 0, l = 0;
     int dmax = 0;
@@ -313,7 +327,7 @@ __global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t c
     atomicMax(&s_dmax, dmax);
     if (threadIdx.x == 0) {
         int64_t rc = 0, rl = 0;
-        for (int t = 0; t < 1024; ++t) {
+        for (int t = 0; t < nt; ++t) {
             const int64_t vc = s_c[t], vl = s_l[t];
             s_c[t] = rc;
             s_l[t] = rl;
@@ -340,19 +354,21 @@ __global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t c
     if (threadIdx.x == 0) A.info->max_depth = s_dmax;
 }
 
+__global__ void __launch_bounds__(1024) batch_scan_kernel(BatchArgs A, int64_t cell_cap) {
+    if (A.info->status & kErrInvalid) return;
+    batch_scan_block(A, cell_cap);
+}
+
+// Every cell of one set with its links, then the set's particles in key
+// order (tiles of T particles; all T threads of the block).
 template <int T>
-__global__ void __launch_bounds__(T, 2048 / T) batch_emit_kernel(BatchArgs A, EmitOut out) {
-    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+__device__ void emit_set(const BatchArgs &A, const EmitOut &out, int set) {
     __shared__ TileSharedT<T> ts;
     __shared__ uint32_t woff[T / 32][kLevelFields];
     __shared__ uint32_t s_run[kLevelFields], s_lvl[kLevelFields], s_tile[kLevelFields];
-    __shared__ int s_q;
-    for (;;) {
-        const int q = take_set(&A.queue[1], A.n_sets, &s_q);
-        if (q < 0) return;
-        const int set = A.order[q];
+    {
         const int64_t o = A.off[set], ns = A.off[set + 1] - o;
-        if (ns <= 0) continue;
+        if (ns <= 0) return;
         const int64_t cell_base = A.set_cell_off[set], leaf_base = A.set_leaf_off[set];
         if (threadIdx.x == 0) {
             uint32_t r = 0;
@@ -392,6 +408,17 @@ __global__ void __launch_bounds__(T, 2048 / T) batch_emit_kernel(BatchArgs A, Em
     }
 }
 
+template <int T>
+__global__ void __launch_bounds__(T, 2048 / T) batch_emit_kernel(BatchArgs A, EmitOut out) {
+    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+    __shared__ int s_q;
+    for (;;) {
+        const int q = take_set(&A.queue[1], A.n_sets, &s_q);
+        if (q < 0) return;
+        emit_set<T>(A, out, A.order[q]);
+    }
+}
+
 // FP64 sum of a leaf too long for the FP32 routes (more than 2^20 members).
 __device__ __noinline__ void leaf_sum_f64_serial(const MomOut &o, const float4 *xs, int64_t c,
                                                  int64_t pf, int64_t pe, bool has64) {
@@ -414,18 +441,15 @@ __device__ __noinline__ void leaf_sum_f64_serial(const MomOut &o, const float4 *
     finish_d(o, c, D, ref, bb, has64);
 }
 
+// Moments of one set: every leaf in key order, then the other cells level by
+// level, deepest first (all threads of the block).
 template <int MODE>
-__global__ void __launch_bounds__(kBMomThreads, 3)
-    batch_moments_kernel(BatchArgs A, TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell) {
-    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+__device__ void moments_set(const BatchArgs &A, const TreeIn &T, const MomOut &o,
+                            const int32_t *__restrict__ leaf_cell, int set) {
     __shared__ int64_t s_lvl[kLevels + 1];
-    __shared__ int s_q;
-    for (;;) {
-        const int q = take_set(&A.queue[2], A.n_sets, &s_q);
-        if (q < 0) return;
-        const int set = A.order[q];
+    {
         const int64_t ns = A.off[set + 1] - A.off[set];
-        if (ns <= 0) continue;
+        if (ns <= 0) return;
         if (threadIdx.x == 0) {
             int64_t r = A.set_cell_off[set];
             for (int d = 0; d < kLevels; ++d) {
@@ -452,15 +476,93 @@ __global__ void __launch_bounds__(kBMomThreads, 3)
     }
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kBMomThreads, 3)
+    batch_moments_kernel(BatchArgs A, TreeIn T, MomOut o, const int32_t *__restrict__ leaf_cell) {
+    if (A.info->status & (kErrOverflow | kErrNonFinite | kErrInvalid)) return;
+    __shared__ int s_q;
+    for (;;) {
+        const int q = take_set(&A.queue[2], A.n_sets, &s_q);
+        if (q < 0) return;
+        moments_set<MODE>(A, T, o, leaf_cell, A.order[q]);
+    }
+}
+
 // The set offsets must partition [0, n_total): off[0] = 0, off[S] = n_total,
 // non-decreasing.  Otherwise every batched kernel skips its work.
-__global__ void set_check_kernel(const int64_t *off, int32_t S, int64_t n_total, DevInfo *info) {
+__device__ void set_check_grid(const int64_t *off, int32_t S, int64_t n_total, DevInfo *info) {
     bool bad = false;
     if (blockIdx.x == 0 && threadIdx.x == 0) bad = (off[0] != 0 || off[S] != n_total);
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
          s += (int64_t)gridDim.x * blockDim.x)
         bad |= off[s + 1] < off[s] || off[s + 1] - off[s] > 2147483647LL;
     if (bad) atomicOr(&info->status, kErrInvalid);
+}
+
+__global__ void set_check_kernel(const int64_t *off, int32_t S, int64_t n_total, DevInfo *info) {
+    set_check_grid(off, S, n_total, info);
+}
+
+// A barrier across every block of a cooperative launch (all blocks are
+// resident at once, so every block arrives).  bar[0] counts arrivals, bar[1]
+// is the generation; the last block to arrive resets the count and opens the
+// next generation.  The wait is bounded: one that runs out records a timeout
+// and lets the block go on.
+__device__ void grid_barrier(uint32_t *bar, int64_t limit, DevInfo *info) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *gen = bar + 1;
+        const uint32_t g = *gen;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            int64_t it = 0;
+            while (*gen == g) {
+                if (!poll_backoff(it, limit)) {
+                    flag_error(&info->status, kErrTimeout);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// The whole batched build in one cooperative launch (fixed cell capacity):
+// offsets checked, sets ordered, every set's front (keys, sort, counts), the
+// offsets of all sets, then each set's cells and moments by the block that
+// takes it -- phases separated by grid barriers.
+template <int T, int MODE>
+__global__ void __launch_bounds__(T, 1024 / T)
+    batch_all_kernel(BatchArgs A, int32_t *order, EmitOut out, TreeIn Tr, MomOut o,
+                     const int32_t *__restrict__ leaf_cell, int64_t n_total, int64_t cell_cap,
+                     int64_t wait_limit) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    uint32_t *bar = A.queue + 4;
+    __shared__ int s_q;
+    set_check_grid(A.off, A.n_sets, n_total, A.info);
+    grid_barrier(bar, wait_limit, A.info);
+    // the status words below were all written before a barrier: every block
+    // reads the same values and takes the same branch
+    if (*(volatile uint32_t *)&A.info->status & kErrInvalid) return;
+    if (blockIdx.x == 0) set_order_block(A.off, A.n_sets, order);
+    grid_barrier(bar, wait_limit, A.info);
+    front_sets<T>(A, raw);
+    grid_barrier(bar, wait_limit, A.info);
+    if (blockIdx.x == 0) batch_scan_block(A, cell_cap);
+    grid_barrier(bar, wait_limit, A.info);
+    if (*(volatile uint32_t *)&A.info->status & (kErrOverflow | kErrNonFinite)) return;
+    for (;;) {
+        const int q = take_set(&A.queue[1], A.n_sets, &s_q);
+        if (q < 0) return;
+        const int set = order[q];
+        emit_set<T>(A, out, set);
+        moments_set<MODE>(A, Tr, o, leaf_cell, set);
+    }
 }
 
 }  // namespace
@@ -540,7 +642,64 @@ cudaError_t launch_batched_t(const BatchArgs &A, int32_t S, int ncrit, tb_tree &
 
 }  // namespace
 
+template <int T, int MODE>
+cudaError_t launch_batched_one_t(const BatchArgs &A, int32_t S, int ncrit, int64_t n_total,
+                                 tb_tree &t, Workspace &ws, int64_t cell_cap, cudaStream_t s) {
+    auto kern = batch_all_kernel<T, MODE>;
+    const size_t smem = batch_front_smem<T>(ncrit);
+    static std::atomic<uint64_t> attr_done{0};
+    if (first_on_device(attr_done)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_front_smem<T>(kMaxNcrit));
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    }
+    int dev = 0, nsm = 152, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    // every block resident at once (the grid barriers need it), at most one
+    // block per set
+    const int grid = S < per_sm * nsm ? (S > 0 ? S : 1) : per_sm * nsm;
+    BatchArgs a = A;
+    int32_t *order = ws.set_order;
+    EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
+                t.leaf_cell, nullptr};
+    TreeIn Tr{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+    MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
+    const int32_t *leaf_cell = t.leaf_cell;
+    int64_t nt = n_total, cap = cell_cap, lim = g_wait_limit;
+    void *args[] = {&a, &order, &out, &Tr, &o, &leaf_cell, &nt, &cap, &lim};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(T), args,
+                                    smem, s);
+    if (e != cudaSuccess) return e;
+    ++g_launches;
+    mark(ws, "batch_all", s);
+    return cudaSuccess;
+}
+
 bool batch_threads_valid(int threads) { return threads == 0 || threads == 512 || threads == 1024; }
+
+cudaError_t launch_batched_one(const float *pos, const float *mass, const int64_t *off, int32_t S,
+                               int64_t n_total, int ncrit, int threads, tb_tree &t, Workspace &ws,
+                               int64_t cell_cap, int mode, cudaStream_t s) {
+    BatchArgs A{pos, mass, off, ws.set_order, S, ncrit, t.pkey, t.perm, ws.keys_alt,
+                ws.perm_alt, ws.xm, ws.xs, ws.ml, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
+                t.set_root, ws.set_ctr, ws.info};
+    const int T = threads ? threads : kBDefaultThreads;
+#define TB_ONE(TT, MM) \
+    if (T == TT && mode == MM) return launch_batched_one_t<TT, MM>(A, S, ncrit, n_total, t, ws, cell_cap, s);
+    TB_ONE(512, TB_MOM_FP32_COMP)
+    TB_ONE(512, TB_MOM_FP32_PLAIN)
+    TB_ONE(512, TB_MOM_FP64)
+    TB_ONE(1024, TB_MOM_FP32_COMP)
+    TB_ONE(1024, TB_MOM_FP32_PLAIN)
+    TB_ONE(1024, TB_MOM_FP64)
+#undef TB_ONE
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *off, int32_t S,
                            int ncrit, int threads, tb_tree &t, Workspace &ws, int64_t cell_cap,

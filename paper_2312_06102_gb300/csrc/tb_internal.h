@@ -107,7 +107,7 @@ struct Workspace {
     int32_t *set_order = nullptr;    // [S] processing order (largest first)
     uint32_t *set_cnt = nullptr;     // [S][kLevelFields] cells per level and leaves of each set
     int64_t *set_leaf_off = nullptr; // [S+1]
-    uint32_t *set_ctr = nullptr;     // [4] work-queue tickets
+    uint32_t *set_ctr = nullptr;     // [8] work-queue tickets, grid-barrier words
 
     cudaStream_t last_stream = nullptr;
     // tree walk scratch and whether the moments match the current structure
@@ -154,6 +154,12 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                            int ncrit, int threads, tb_tree &t, Workspace &ws, int64_t cell_cap,
                            int phase, int mode, cudaStream_t s);
 bool batch_threads_valid(int threads);   // 0 (default), 512 or 1024
+// The whole batched build (fixed cell capacity) in one cooperative launch;
+// an error return leaves nothing enqueued, and the caller may fall back to
+// the multi-launch path.
+cudaError_t launch_batched_one(const float *pos, const float *mass, const int64_t *off, int32_t S,
+                               int64_t n_total, int ncrit, int threads, tb_tree &t, Workspace &ws,
+                               int64_t cell_cap, int mode, cudaStream_t s);
 cudaError_t launch_set_check(const int64_t *off, int32_t S, int64_t n_total, Workspace &ws,
                              cudaStream_t s);
 

@@ -93,6 +93,29 @@ def test_batched_mixed_sizes(n_crit, threads):
     _check_sets(t, pos, mass, offsets, n_crit)
 
 
+@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batched_one_launch_equals_separate_launches(threads, mode):
+    """The cooperative one-launch build gives the same arrays as the separate
+    launches, for both block sizes and every moment mode."""
+    m = tb()
+    sizes = [700, 3000, 50_000, 1, 0, 9999, 4096, 65_536]
+    pos, mass, offsets = _sets(sizes, 9)
+    a, p, w, off = _run(pos, mass, offsets, mode=mode, threads=threads)
+    cap = a.n_cells + 16
+    b = m.build_batched(p, w, off, cell_capacity=cap, mom_mode=mode, batch_threads=threads,
+                        one_launch=True)
+    torch.cuda.synchronize()
+    assert b.sync() == 0 and b.n_cells == a.n_cells
+    keys = ["pkey", "perm", "ckey", "level", "parent", "child_first", "child_end", "pfirst",
+            "pend", "mass", "com", "com_lo", "quad", "aabb"] + (["mass64", "com64", "quad64"]
+                                                                if mode == 2 else [])
+    for k in keys:
+        assert np.array_equal(to_np(getattr(a, k)), to_np(getattr(b, k))), k
+    if mode != 1:   # plain FP32 is reported, not held to the tolerances
+        _check_sets(b, pos, mass, offsets, 16, mode=mode)
+
+
 def test_batched_block_sizes_agree():
     """512- and 1024-thread builds of the same sets give identical arrays."""
     sizes = [700, 3000, 50_000, 1, 9999]
@@ -119,20 +142,25 @@ def test_batched_plummer_sets_sampled():
     _check_sets(t, b.pos, b.mass, b.offsets, 16, sets=sorted(rng.choice(512, 40, replace=False)))
 
 
-def test_batched_graph_replay_with_jitter():
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batched_graph_replay_with_jitter(one_launch):
     """Capacity mode needs no host sync; captured in a CUDA graph and replayed
-    on jittered positions (steps 1 and 3), each matching the oracle."""
+    on jittered positions (steps 1 and 3), each matching the oracle -- as
+    separate launches, or as one cooperative launch."""
     m = tb()
     b = batched_plummer(n_sets=64, seed=4)
     t, p, w, off = _run(b.pos, b.mass, b.offsets)
     cap = int(t.n_cells * 1.2) + 64
-    m.build_batched(p, w, off, cell_capacity=cap, tree=t)
+    m.build_batched(p, w, off, cell_capacity=cap, tree=t, one_launch=one_launch)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
+        n0 = m.kernel_launches()
         with torch.cuda.graph(g, stream=s):
-            m.build_batched(p, w, off, cell_capacity=cap, tree=t, stream=s)
+            m.build_batched(p, w, off, cell_capacity=cap, tree=t, stream=s, one_launch=one_launch)
+        if one_launch:
+            assert m.kernel_launches() - n0 == 1
     for step in (1, 3):
         jit = jitter_offsets(4, step, b.offsets, b.scale)
         pj = (b.pos + jit).astype(np.float32)
