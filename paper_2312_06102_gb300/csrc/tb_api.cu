@@ -75,7 +75,6 @@ void free_cells(TreeState &S) {
     dev_free(t.child_end); dev_free(t.pfirst); dev_free(t.pend);
     dev_free(t.mass); dev_free(t.com); dev_free(t.com_lo); dev_free(t.quad); dev_free(t.aabb);
     dev_free(t.mass64); dev_free(t.com64); dev_free(t.quad64);
-    dev_free(S.ws.int_list);
     t.cell_capacity = 0;
     S.ws.cell_cap = 0;
 }
@@ -147,13 +146,15 @@ tb_status ensure_cells(TreeState &S, int64_t cells, bool fp64) {
     if (cells > ws.cell_cap || (fp64 && !t.mass64)) {
         cudaDeviceSynchronize();
         int64_t cap = cells > ws.cell_cap ? cells : ws.cell_cap;
+        // the parent pass bulk-copies children's moments in whole groups of
+        // four cells, up to three cells past the last one
+        const int64_t pad = kMomentPad;
         free_cells(S);
         if (!dev_alloc(t.ckey, cap) || !dev_alloc(t.level, cap) || !dev_alloc(t.parent, cap) ||
             !dev_alloc(t.child_first, cap) || !dev_alloc(t.child_end, cap) ||
-            !dev_alloc(t.pfirst, cap) || !dev_alloc(t.pend, cap) || !dev_alloc(t.mass, cap) ||
-            !dev_alloc(t.com, 3 * cap) || !dev_alloc(t.com_lo, 3 * cap) ||
-            !dev_alloc(t.quad, 6 * cap) || !dev_alloc(t.aabb, 6 * cap) ||
-            !dev_alloc(ws.int_list, cap))
+            !dev_alloc(t.pfirst, cap) || !dev_alloc(t.pend, cap) || !dev_alloc(t.mass, cap + pad) ||
+            !dev_alloc(t.com, 3 * (cap + pad)) || !dev_alloc(t.com_lo, 3 * (cap + pad)) ||
+            !dev_alloc(t.quad, 6 * (cap + pad)) || !dev_alloc(t.aabb, 6 * (cap + pad)))
             return TB_ENOMEM;
         if (fp64 && (!dev_alloc(t.mass64, cap) || !dev_alloc(t.com64, 3 * cap) ||
                      !dev_alloc(t.quad64, 6 * cap)))

@@ -470,7 +470,7 @@ __device__ void moments_set(const BatchArgs &A, const TreeIn &T, const MomOut &o
         __syncthreads();
         for (int d = kDepthMax - 1; d >= 0; --d) {
             for (int64_t c = s_lvl[d] + threadIdx.x; c < s_lvl[d + 1]; c += blockDim.x)
-                if (T.child_first[c] >= 0) combine_children<MODE>(T, o, c);
+                if (T.child_first[c] >= 0) combine_children<MODE>(T, o, c, cells_of(o));
             __syncthreads();
         }
     }
@@ -612,7 +612,7 @@ cudaError_t launch_batched_t(const BatchArgs &A, int32_t S, int ncrit, tb_tree &
         return cudaSuccess;
     }
     EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-                t.leaf_cell, nullptr};
+                t.leaf_cell};
     // the emission keeps 1024-thread tiles whatever the front's block size
     // (two blocks per SM at 32 registers): measured faster than 512 (0.96
     // against 1.10 ms on the 4,096-set workload)
@@ -620,7 +620,7 @@ cudaError_t launch_batched_t(const BatchArgs &A, int32_t S, int ncrit, tb_tree &
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark(ws, "batch_emit", s);
-    TreeIn Tr{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+    TreeIn Tr{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf, t.parent};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
     const int grid_mom = fit(3);
     switch (mode) {
@@ -666,8 +666,8 @@ cudaError_t launch_batched_one_t(const BatchArgs &A, int32_t S, int ncrit, int64
     BatchArgs a = A;
     int32_t *order = ws.set_order;
     EmitOut out{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-                t.leaf_cell, nullptr};
-    TreeIn Tr{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+                t.leaf_cell};
+    TreeIn Tr{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf, t.parent};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
     const int32_t *leaf_cell = t.leaf_cell;
     int64_t nt = n_total, cap = cell_cap, lim = g_wait_limit;

@@ -305,8 +305,6 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __shared__ uint32_t s_entry[kEfTile];               // k - s | m << 11 | L << 16 | Lprev << 21
     __shared__ uint32_t s_mask[kEfChunks][kLevels];     // level masks of each chunk of 32 starts
     __shared__ uint32_t s_cpre[kEfChunks][kLevels];     // starts of each level in earlier chunks
-    __shared__ uint32_t s_ipre[kEfChunks][kLevels];     // non-leaf cells of each level in earlier chunks
-    __shared__ uint32_t s_ibase[kLevels];               // the block's first slot in each level's list
     __shared__ uint32_t s_base[kLevelFields];           // first level-d cell (leaf) of the block
     __shared__ uint32_t s_wcnt[kEfWarps];
     __shared__ uint8_t s_Llast[kEfThreads];
@@ -374,9 +372,7 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __syncthreads();
     const int total = (int)s_total;
     const int nchunks = (total + 31) / 32;
-    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose).  A
-    // start opens a non-leaf cell at level d iff it opens cells at d and at
-    // d + 1 (m <= d < L), so the non-leaf masks are s_mask[d] & s_mask[d + 1].
+    // level masks of every chunk of 32 starts (a 32 x 32 bit transpose)
     for (int c = warp; c < nchunks; c += kEfWarps) {
         const int i = c * 32 + lane;
         uint32_t v = 0;
@@ -395,20 +391,12 @@ __global__ void __launch_bounds__(kEfThreads, 2)
         if (lane < kLevels) s_mask[c][lane] = v;
     }
     __syncthreads();
-    auto imask = [&](int c, int d) {
-        return d + 1 < kLevels ? s_mask[c][d] & s_mask[c][d + 1] : 0u;
-    };
     if (threadIdx.x < kLevels) {
-        uint32_t r = 0, ri = 0;
+        uint32_t r = 0;
         for (int c = 0; c < nchunks; ++c) {
             s_cpre[c][threadIdx.x] = r;
             r += __popc(s_mask[c][threadIdx.x]);
-            s_ipre[c][threadIdx.x] = ri;
-            ri += __popc(imask(c, threadIdx.x));
         }
-        // the block's slots in the level's list of non-leaf cells (their
-        // order in the list is immaterial: each is combined on its own)
-        s_ibase[threadIdx.x] = ri ? atomicAdd(&info_w->int_cnt[threadIdx.x], ri) : 0u;
     }
     __syncthreads();
     const unsigned lt = lanemask_lt();
@@ -435,9 +423,6 @@ __global__ void __launch_bounds__(kEfThreads, 2)
             out.pfirst[idx] = (int32_t)k;
             out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == mm ? 1 : 0);
             out.child_first[idx] = (d < LL) ? (int32_t)P(d + 1) : -1;
-            if (d < LL)
-                out.int_list[info->level_offset[d] + s_ibase[d] + s_ipre[c][d] +
-                             (uint32_t)__popc(imask(c, d) & lt)] = (int32_t)idx;
         }
         out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)P(LL);
     }
@@ -488,7 +473,7 @@ cudaError_t launch_emit(const uint64_t *skeys, int64_t n, int ncrit, Workspace &
     (void)ncrit;
     const int64_t tiles = (n + kLvTile - 1) / kLvTile;
     EmitOut o{t.ckey, t.level, t.parent, t.child_first, t.child_end, t.pfirst, t.pend,
-              t.leaf_cell, ws.int_list};
+              t.leaf_cell};
     const int64_t blocks = (n + kEfTile - 1) / kEfTile;
     emit_starts_kernel<<<(unsigned)blocks, kEfThreads, 0, s>>>(skeys, ws.ml, n, ws.level_cnt, tiles,
                                                                ws.info, o);

@@ -168,7 +168,6 @@ struct EmitOut {
     uint8_t *level;
     int32_t *parent, *child_first, *child_end, *pfirst, *pend;
     int32_t *leaf_cell;
-    int32_t *int_list;   // single tree: the non-leaf cells of each level, listed
 };
 
 // Cells opened and closed by one particle.  P(d) is the global index of the

@@ -18,6 +18,7 @@ constexpr int kLevelFields = kLevels + 1;   // 22 level counters + 1 leaf counte
 constexpr int kMaxNcrit = 1024;
 constexpr int64_t kMaxCells = 2147483647;   // cell indices are int32
 constexpr int64_t kBigCell = int64_t(1) << 20;   // cells above this are summed in FP64
+constexpr int64_t kMomentPad = 8;   // cells allocated past the capacity in the moment arrays
 
 // device status bits (tb_dev_info::status)
 constexpr uint32_t kErrNonFinite = 1u;
@@ -46,7 +47,6 @@ struct DevInfo {
     uint32_t misc_ctr[8];         // [0] bbox blocks done, [1] level-scan blocks done,
                                   // [2] big-leaf queue length, [3] big-leaf tickets,
                                   // [4] key blocks done, [5] long sort runs, [6] their tickets
-    uint32_t int_cnt[kLevels];    // non-leaf cells of each level listed by the emission
 };
 
 // Sort tuning: a compiled variant.
@@ -88,7 +88,6 @@ struct Workspace {
     float *bbox_part = nullptr;      // [blocks][8]
     uint32_t *level_cnt = nullptr;   // [level tiles][kLevelFields]
     uint16_t *ml = nullptr;          // [n] m_k | L_k << 8 of each sorted particle
-    int32_t *int_list = nullptr;     // [cells] non-leaf cells of level d at [level_offset[d], ...)
     int32_t *long_runs = nullptr;    // [n / 1024 + 2] sort runs too long for the run step
     int32_t *big_leaf = nullptr;     // [n] queue of depth-21 leaves too long for one thread
     DevInfo *info = nullptr;

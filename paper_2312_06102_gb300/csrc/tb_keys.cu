@@ -161,7 +161,6 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
         info->epoch = (info->epoch + 16u) & 0x3fffffffu;
         for (int p = 0; p < 16; ++p) info->sort_tile_ctr[p] = 0;
         for (int p = 1; p < 8; ++p) info->misc_ctr[p] = 0;
-        for (int d = 0; d < kLevels; ++d) info->int_cnt[d] = 0;
         info->n_cells = 0;
         info->n_leaves = 0;
         info->max_depth = 0;

@@ -11,9 +11,10 @@
 //                          through the permutation;
 //   big_leaf_kernel      : depth-21 leaves of identical keys that are too long
 //                          for one thread, summed block-wide;
-//   level_moments_kernel : one launch per level, deepest first: every non-leaf
-//                          cell (listed per level by the emission) combines
-//                          its children, which earlier launches finished.
+//   level_moments_kernel : one launch per level, deepest first: the children
+//                          of the level, in tiles bulk-copied (TMA) into
+//                          shared memory, and every non-leaf cell of the
+//                          level combined from its tile.
 //
 // Moments of a cell: M = sum m; centre of mass c = sum m x / M; central
 // second moment Q = sum m (x - c)(x - c)^T (6 components xx xy xz yy yz zz);
@@ -329,19 +330,116 @@ __global__ void __launch_bounds__(kMomThreads, 4)
     }
 }
 
-// The non-leaf cells of level d, from their children (finished by the
-// launch for level d + 1, or by the leaf launches).  The emission listed
-// them per level, so every lane takes one.
+// Non-leaf cells of level d from their children at level d + 1, which the
+// leaf launches or the launch for level d + 1 finished.  The children of
+// consecutive cells are consecutive cells, so level d + 1 is cut into tiles
+// of kLmTile children: a block bulk-copies (TMA) the FP32 moments of its
+// tile -- plus the few children past it that belong to its last parents --
+// into shared memory, and combines there every parent whose first child
+// lies in the tile.  Each copy covers whole groups of four cells, so that
+// every array's piece starts on a 16-byte boundary; the moment arrays are
+// allocated kMomentPad cells past the capacity, which the rounding never
+// passes.  Blocks loop over the tiles of the level (one persistent grid per
+// launch).
+constexpr int kLmThreads = 128;
+constexpr int kLmTile = 512;
+constexpr int kLmSpan = kLmTile + 16;   // 3 before the tile, 7 past it, rounding to 4
+
+struct LevelSmem {
+    float mass[kLmSpan];
+    float com[3 * kLmSpan];
+    float com_lo[3 * kLmSpan];
+    float quad[6 * kLmSpan];
+    float aabb[6 * kLmSpan];
+    int32_t own[kLmTile];                     // parents whose first child is in the tile
+    uint32_t wcount[kLmThreads / 32];
+    uint64_t bar;
+};
+static_assert(kLmSpan % 4 == 0, "each staged array spans whole 16-byte groups");
+
+// Children's FP32 moments staged in shared memory: cell c at slot c - base.
+struct CellsStaged {
+    const LevelSmem *S;
+    int64_t base;
+    __device__ __forceinline__ float m(int64_t c) const { return S->mass[c - base]; }
+    __device__ __forceinline__ float x(int64_t c, int a) const { return S->com[3 * (c - base) + a]; }
+    __device__ __forceinline__ float xl(int64_t c, int a) const { return S->com_lo[3 * (c - base) + a]; }
+    __device__ __forceinline__ float2 q2(int64_t c, int i) const {
+        return reinterpret_cast<const float2 *>(S->quad + 6 * (c - base))[i];
+    }
+    __device__ __forceinline__ float2 b2(int64_t c, int i) const {
+        return reinterpret_cast<const float2 *>(S->aabb + 6 * (c - base))[i];
+    }
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(kMomThreads, 4)
-    level_moments_kernel(TreeIn T, MomOut o, const int32_t *__restrict__ int_list, DevInfo *info,
-                         int d) {
-    if (info->status & (kErrOverflow | kErrNonFinite)) return;
-    const int64_t cnt = info->int_cnt[d];
-    const int32_t *list = int_list + info->level_offset[d];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < cnt; q += stride)
-        combine_children<MODE>(T, o, list[q]);
+__global__ void __launch_bounds__(kLmThreads, 5)
+    level_moments_kernel(TreeIn T, MomOut o, DevInfo *info, int d, int64_t wait_limit) {
+    if (info->status & (kErrOverflow | kErrNonFinite | kErrTimeout)) return;
+    extern __shared__ __align__(128) unsigned char lm_raw[];
+    LevelSmem &S = *reinterpret_cast<LevelSmem *>(lm_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t off1 = info->level_offset[d + 1], off2 = info->level_offset[d + 2];
+    const int64_t tiles = (off2 - off1 + kLmTile - 1) / kLmTile;
+    if ((int64_t)blockIdx.x >= tiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t c_lo = off1 + t * kLmTile, c_hi = min64(c_lo + kLmTile, off2);
+        const int64_t s_lo = c_lo & ~int64_t(3);
+        const int64_t s_hi = (min64(c_hi + 7, off2) + 3) & ~int64_t(3);
+        if (threadIdx.x == 0) {
+            const uint32_t len = (uint32_t)(s_hi - s_lo);
+            mbar_arrive_expect_tx(&S.bar, len * 76u);
+            bulk_load(S.mass, o.mass + s_lo, len * 4u, &S.bar);
+            bulk_load(S.com, o.com + 3 * s_lo, len * 12u, &S.bar);
+            bulk_load(S.com_lo, o.com_lo + 3 * s_lo, len * 12u, &S.bar);
+            bulk_load(S.quad, o.quad + 6 * s_lo, len * 24u, &S.bar);
+            bulk_load(S.aabb, o.aabb + 6 * s_lo, len * 24u, &S.bar);
+        }
+        // while the copies fly: the parents whose first child is in the tile
+        // (a child is the first of its parent iff the parent differs from
+        // the previous cell's), listed in order
+        const int nt = (int)(c_hi - c_lo);
+        uint32_t before = 0;
+        for (int x0 = 0; x0 < nt; x0 += kLmThreads) {
+            const int x = x0 + (int)threadIdx.x;
+            int32_t p = -1;
+            bool first = false;
+            if (x < nt) {
+                const int64_t c = c_lo + x;
+                p = T.parent[c];
+                first = (c == off1) || T.parent[c - 1] != p;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, first);
+            if (lane == 0) S.wcount[warp] = __popc(b);
+            __syncthreads();
+            uint32_t pre = before;
+            for (int w = 0; w < warp; ++w) pre += S.wcount[w];
+            if (first) S.own[pre + __popc(b & lanemask_lt())] = p;
+            for (int w = 0; w < kLmThreads / 32; ++w) before += S.wcount[w];
+            __syncthreads();
+        }
+        const bool ok = mbar_wait_bounded(&S.bar, phase, wait_limit);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                flag_error(&info->status, kErrTimeout);
+                mbar_wait_bounded(&S.bar, phase ^ 1u, wait_limit);
+            }
+            return;
+        }
+        const CellsStaged src{&S, s_lo};
+        for (uint32_t i = threadIdx.x; i < before; i += kLmThreads)
+            combine_children<MODE>(T, o, S.own[i], src);
+        // the next tile's copies overwrite what this one read
+        fence_proxy_async_smem();
+        __syncthreads();
+    }
 }
 
 // Block-wide sums of the long depth-21 leaves queued by the leaf launch.
@@ -475,7 +573,7 @@ __global__ void wait_selftest_kernel(int64_t limit, uint32_t *status, const uint
 
 template <int MODE>
 cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
-    TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf};
+    TreeIn T{t.child_first, t.child_end, t.pfirst, t.pend, ws.big_leaf, t.parent};
     MomOut o{t.mass, t.com, t.com_lo, t.quad, t.aabb, t.mass64, t.com64, t.quad64};
     const int64_t n = t.n_particles;
     // misc_ctr[2..3]: big-leaf queue and tickets; [5]: long-leaf queue
@@ -486,6 +584,11 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
         cudaFuncSetAttribute(leaf_tile_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)leaf_tile_smem());
         cudaFuncSetAttribute(leaf_tile_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(level_moments_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LevelSmem));
+        cudaFuncSetAttribute(level_moments_kernel<MODE>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     }
     // the long-leaf queue (at most n / 2 leaves of two or more members past
@@ -509,13 +612,14 @@ cudaError_t moments_impl(tb_tree &t, Workspace &ws, cudaStream_t s) {
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark(ws, "leaves", s);
-    // one persistent grid per launch; a level holds at most n cells
-    int64_t grid = (n + kMomThreads - 1) / kMomThreads;
-    if (grid > 152 * 8) grid = 152 * 8;
+    // one persistent grid per launch: five blocks per SM, never more than
+    // the tiles a level of at most n cells can have
+    int64_t grid = (n + kLmTile - 1) / kLmTile;
+    if (grid > 152 * 5) grid = 152 * 5;
     if (grid < 1) grid = 1;
     for (int d = kDepthMax - 1; d >= 0; --d) {
-        level_moments_kernel<MODE><<<(unsigned)grid, kMomThreads, 0, s>>>(T, o, ws.int_list,
-                                                                           ws.info, d);
+        level_moments_kernel<MODE><<<(unsigned)grid, kLmThreads, sizeof(LevelSmem), s>>>(
+            T, o, ws.info, d, g_wait_limit);
         ++g_launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

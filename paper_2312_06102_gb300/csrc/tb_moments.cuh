@@ -23,7 +23,28 @@ struct MomOut {
 struct TreeIn {
     const int32_t *child_first, *child_end, *pfirst, *pend;
     int32_t *big_leaf;
+    const int32_t *parent;   // each cell's parent, -1 for the root
 };
+
+// The FP32 moments of cells (mass, centre of mass and its low part, second
+// moment, bounding box) as a parent's combination reads its children's:
+// straight from the tree's arrays ...
+struct CellsGlobal {
+    const float *mass, *com, *com_lo, *quad, *aabb;
+    __device__ __forceinline__ float m(int64_t c) const { return mass[c]; }
+    __device__ __forceinline__ float x(int64_t c, int a) const { return com[3 * c + a]; }
+    __device__ __forceinline__ float xl(int64_t c, int a) const { return com_lo[3 * c + a]; }
+    // rows of six (xx xy xz yy yz zz; lo xyz hi xyz) as three float2
+    __device__ __forceinline__ float2 q2(int64_t c, int i) const {
+        return reinterpret_cast<const float2 *>(quad + 6 * c)[i];
+    }
+    __device__ __forceinline__ float2 b2(int64_t c, int i) const {
+        return reinterpret_cast<const float2 *>(aabb + 6 * c)[i];
+    }
+};
+__device__ __forceinline__ CellsGlobal cells_of(const MomOut &o) {
+    return {o.mass, o.com, o.com_lo, o.quad, o.aabb};
+}
 
 __device__ __forceinline__ int qidx(int a, int b) {
     // xx xy xz yy yz zz
@@ -427,11 +448,12 @@ __device__ void leaf_sum(const MomOut &o, Src xs, int64_t c, int64_t pf, int64_t
 
 // Offset of child c's centre from the reference point ref, as a
 // double-float (h, l): (com_c - ref) + com_lo_c.
-__device__ __forceinline__ void child_offset(const MomOut &o, int64_t c, int a, float ref, float &h,
+template <class Src>
+__device__ __forceinline__ void child_offset(const Src &o, int64_t c, int a, float ref, float &h,
                                              float &l) {
     float u, v;
-    two_sum(o.com[3 * c + a], -ref, u, v);
-    v = __fadd_rn(v, o.com_lo[3 * c + a]);
+    two_sum(o.x(c, a), -ref, u, v);
+    v = __fadd_rn(v, o.xl(c, a));
     fast_two_sum(u, v, h, l);
 }
 
@@ -479,13 +501,18 @@ __device__ __noinline__ void combine_f64(const MomOut &o, int64_t p, int32_t c0,
         write_cell_f64(o, p, M, com, Q, bb, MODE == TB_MOM_FP64);
 }
 
-template <int MODE>
-__device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
+// Parent p from its children, whose FP32 moments come from `src` (the tree's
+// arrays, or a copy staged in shared memory); the FP64 route reads the tree's
+// arrays.
+template <int MODE, class Src>
+__device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p, const Src &src) {
     const int32_t c0 = T.child_first[p], c1 = T.child_end[p];
-    // six floats of cell c (quad, aabb: rows of 24 bytes, 8-byte aligned)
-    auto row6 = [](const float *base, int64_t c, float v[6]) {
-        const float2 *r = reinterpret_cast<const float2 *>(base + 6 * c);
-        const float2 x = r[0], y = r[1], z = r[2];
+    auto qrow = [&](int64_t c, float v[6]) {
+        const float2 x = src.q2(c, 0), y = src.q2(c, 1), z = src.q2(c, 2);
+        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y; v[4] = z.x; v[5] = z.y;
+    };
+    auto brow = [&](int64_t c, float v[6]) {
+        const float2 x = src.b2(c, 0), y = src.b2(c, 1), z = src.b2(c, 2);
         v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y; v[4] = z.x; v[5] = z.y;
     };
     auto grow = [](float bb[6], const float cb[6]) {
@@ -495,7 +522,7 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
         }
     };
     float bb[6];
-    row6(o.aabb, c0, bb);
+    brow(c0, bb);
     const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
     if constexpr (MODE == TB_MOM_FP32_COMP) {
         if (!big) {
@@ -503,18 +530,18 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
             // child's centre, then the shift to the centre of mass (as for a
             // leaf)
             float ref[3];
-            for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
+            for (int a = 0; a < 3; ++a) ref[a] = src.x(c0, a);
             AccS A;
             A.init();
             for (int32_t c = c0; c < c1; ++c) {
                 float h[3], l[3], q[6], cb[6];
-                for (int a = 0; a < 3; ++a) child_offset(o, c, a, ref[a], h[a], l[a]);
-                row6(o.quad, c, q);
+                for (int a = 0; a < 3; ++a) child_offset(src, c, a, ref[a], h[a], l[a]);
+                qrow(c, q);
                 if (c > c0) {
-                    row6(o.aabb, c, cb);
+                    brow(c, cb);
                     grow(bb, cb);
                 }
-                A.add_cell(o.mass[c], h, l, q);
+                A.add_cell(src.m(c), h, l, q);
             }
             finish_s(o, p, A, ref, bb);
             return;
@@ -522,29 +549,30 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p) {
     }
     for (int32_t c = c0 + 1; c < c1; ++c) {
         float cb[6];
-        row6(o.aabb, c, cb);
+        brow(c, cb);
         grow(bb, cb);
     }
     if (MODE == TB_MOM_FP64 || big) {
         combine_f64<MODE>(o, p, c0, c1, bb);
     } else {
         float ref[3];
-        for (int a = 0; a < 3; ++a) ref[a] = o.com[3 * (int64_t)c0 + a];
+        for (int a = 0; a < 3; ++a) ref[a] = src.x(c0, a);
         float M = 0.f, S[3] = {0, 0, 0};
         for (int32_t c = c0; c < c1; ++c) {
-            float m = o.mass[c];
+            float m = src.m(c);
             M += m;
-            for (int a = 0; a < 3; ++a) S[a] += m * (o.com[3 * (int64_t)c + a] - ref[a]);
+            for (int a = 0; a < 3; ++a) S[a] += m * (src.x(c, a) - ref[a]);
         }
         float r[3];
         for (int a = 0; a < 3; ++a) r[a] = (M != 0.f) ? S[a] / M : 0.f;
         float Q[6] = {0, 0, 0, 0, 0, 0};
         for (int32_t c = c0; c < c1; ++c) {
-            float m = o.mass[c], e[3];
-            for (int a = 0; a < 3; ++a) e[a] = (o.com[3 * (int64_t)c + a] - ref[a]) - r[a];
+            float m = src.m(c), e[3], qc[6];
+            for (int a = 0; a < 3; ++a) e[a] = (src.x(c, a) - ref[a]) - r[a];
+            qrow(c, qc);
             int q = 0;
             for (int a = 0; a < 3; ++a)
-                for (int b = a; b < 3; ++b, ++q) Q[q] += o.quad[6 * (int64_t)c + q] + m * e[a] * e[b];
+                for (int b = a; b < 3; ++b, ++q) Q[q] += qc[q] + m * e[a] * e[b];
         }
         float ch[3], cl[3];
         for (int a = 0; a < 3; ++a) { ch[a] = ref[a] + r[a]; cl[a] = 0.f; }

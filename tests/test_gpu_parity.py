@@ -335,6 +335,43 @@ def test_deterministic_repeat():
             assert np.array_equal(to_np(getattr(t1, k)), v), k
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_moments_repeat_on_one_build(mode):
+    """Parents are combined by the last of their children to finish, which
+    counts arrivals per cell and clears the count as it combines: calling
+    tb_moments again on the same build gives the same moments bit for bit.
+    Identical particles add a leaf of 3,000 (block-summed) and one of 300
+    (past the leaf tile's halo, summed from the queue), whose ancestors are
+    combined from those launches."""
+    pos, mass = clustered_halos(1 << 16, 21, n_halo=40)
+    pos = np.concatenate([pos, np.full((3000, 3), pos[5], np.float32),
+                          np.full((300, 3), pos[7], np.float32)])
+    mass = np.concatenate([mass, np.full(3300, mass[3], np.float32)])
+    if mode == 1:
+        # plain FP32: errors are reported, not bounded (as for the other plain-mode test)
+        o = oracle.build_tree(pos, 8)
+        t, p, w = gpu_tree(pos, mass, 8, mode=1)
+        assert_structure_equal(t, o)
+        M, com, quad, aabb = oracle.moments(o, pos, mass)
+        em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+        assert bb_ok and em.max() < 1e-4
+    else:
+        t, o = _check(pos, mass, 8, mode=mode)
+    m = tb()
+    p = torch.from_numpy(pos).cuda()
+    w = torch.from_numpy(mass).cuda()
+    keys = ("mass", "com", "com_lo", "quad", "aabb") + (("mass64", "com64", "quad64") if mode == 2 else ())
+    m.moments(t, p, w)
+    torch.cuda.synchronize()
+    a = {k: to_np(getattr(t, k)).copy() for k in keys}
+    for _ in range(2):
+        m.moments(t, p, w)
+        torch.cuda.synchronize()
+        assert t.sync() == 0
+        for k, v in a.items():
+            assert np.array_equal(to_np(getattr(t, k)), v), k
+
+
 def test_bounded_wait_times_out():
     m = tb()
     assert m.STATUS[m.selftest_wait(1000)] == "TB_ETIMEOUT"
