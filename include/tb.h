@@ -184,8 +184,9 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
  * (new contents written in between are not seen: the moments are those of
  * the particles the tree was built from).  So once the build's work on the
  * stream has completed, the caller may refill those arrays, e.g. with the
- * next step's copy.  Other pointers are read afresh.  Cells of more than 2^20
- * particles are summed in FP64 in every mode.  Returns TB_EINVAL when the
+ * next step's copy.  Other pointers are read afresh.  Leaves of more than
+ * 2^20 particles are summed in FP64 in every mode (parents of that many in
+ * the FP32-plain mode too).  Returns TB_EINVAL when the
  * tree's last tb_build returned an error before it enqueued every stage. */
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
 

@@ -146,11 +146,11 @@ tb_status ensure_cells(TreeState &S, int64_t cells, bool fp64) {
     if (cells > ws.cell_cap || (fp64 && !t.mass64)) {
         cudaDeviceSynchronize();
         int64_t cap = cells > ws.cell_cap ? cells : ws.cell_cap;
-        // the parent pass bulk-copies children's moments in whole groups of
-        // four cells, up to three cells past the last one
+        // the parent pass bulk-copies children's moments and parent links in
+        // whole groups of four cells, up to three cells past the last one
         const int64_t pad = kMomentPad;
         free_cells(S);
-        if (!dev_alloc(t.ckey, cap) || !dev_alloc(t.level, cap) || !dev_alloc(t.parent, cap) ||
+        if (!dev_alloc(t.ckey, cap) || !dev_alloc(t.level, cap) || !dev_alloc(t.parent, cap + pad) ||
             !dev_alloc(t.child_first, cap) || !dev_alloc(t.child_end, cap) ||
             !dev_alloc(t.pfirst, cap) || !dev_alloc(t.pend, cap) || !dev_alloc(t.mass, cap + pad) ||
             !dev_alloc(t.com, 3 * (cap + pad)) || !dev_alloc(t.com_lo, 3 * (cap + pad)) ||

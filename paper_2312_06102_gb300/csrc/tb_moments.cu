@@ -30,8 +30,9 @@
 //                 cannot hold a deep cell's centre to 2e-6 of its side);
 //   FP32_PLAIN -- uncompensated FP32, com_lo = 0;
 //   FP64       -- FP64 accumulation; FP64 outputs beside the FP32 ones.
-// A cell of more than 2^20 particles is summed / combined in FP64 in every
-// mode.
+// A leaf of more than 2^20 particles is summed in FP64 in every mode, and so
+// is a parent of that many in the FP32-plain mode; compensated parents stay
+// in FP32 at every size (their error is relative to their own mass and side).
 #include "tb_moments.cuh"
 
 namespace tb {
@@ -333,14 +334,15 @@ __global__ void __launch_bounds__(kMomThreads, 4)
 // Non-leaf cells of level d from their children at level d + 1, which the
 // leaf launches or the launch for level d + 1 finished.  The children of
 // consecutive cells are consecutive cells, so level d + 1 is cut into tiles
-// of kLmTile children: a block bulk-copies (TMA) the FP32 moments of its
-// tile -- plus the few children past it that belong to its last parents --
-// into shared memory, and combines there every parent whose first child
-// lies in the tile.  Each copy covers whole groups of four cells, so that
-// every array's piece starts on a 16-byte boundary; the moment arrays are
-// allocated kMomentPad cells past the capacity, which the rounding never
-// passes.  Blocks loop over the tiles of the level (one persistent grid per
-// launch).
+// of kLmTile children: a block bulk-copies (TMA) the FP32 moments and the
+// parent links of its tile -- plus the few children past it that belong to
+// its last parents -- into shared memory, lists the parents whose first
+// child lies in the tile (a child is the first of its parent iff its parent
+// differs from the previous cell's), and combines them there.  Each copy
+// covers whole groups of four cells, so that every array's piece starts on a
+// 16-byte boundary; the moment and parent arrays are allocated kMomentPad
+// cells past the capacity, which the rounding never passes.  Blocks loop
+// over the tiles of the level (one persistent grid per launch).
 constexpr int kLmThreads = 128;
 constexpr int kLmTile = 512;
 constexpr int kLmSpan = kLmTile + 16;   // 3 before the tile, 7 past it, rounding to 4
@@ -351,11 +353,13 @@ struct LevelSmem {
     float com_lo[3 * kLmSpan];
     float quad[6 * kLmSpan];
     float aabb[6 * kLmSpan];
+    int32_t par[kLmSpan + 4];                 // parents of the staged cells and of 4 before
     int32_t own[kLmTile];                     // parents whose first child is in the tile
     uint32_t wcount[kLmThreads / 32];
     uint64_t bar;
 };
 static_assert(kLmSpan % 4 == 0, "each staged array spans whole 16-byte groups");
+static_assert(kLmTile == 4 * kLmThreads, "the listing takes four children per thread");
 
 // Children's FP32 moments staged in shared memory: cell c at slot c - base.
 struct CellsStaged {
@@ -392,37 +396,19 @@ __global__ void __launch_bounds__(kLmThreads, 5)
         const int64_t c_lo = off1 + t * kLmTile, c_hi = min64(c_lo + kLmTile, off2);
         const int64_t s_lo = c_lo & ~int64_t(3);
         const int64_t s_hi = (min64(c_hi + 7, off2) + 3) & ~int64_t(3);
+        // parent links from one group of four before s_lo (the cell before
+        // c_lo), or from the level's start
+        const int64_t p_lo = s_lo >= off1 + 4 ? s_lo - 4 : (off1 & ~int64_t(3));
         if (threadIdx.x == 0) {
             const uint32_t len = (uint32_t)(s_hi - s_lo);
-            mbar_arrive_expect_tx(&S.bar, len * 76u);
+            const uint32_t plen = (uint32_t)(s_hi - p_lo);
+            mbar_arrive_expect_tx(&S.bar, len * 76u + plen * 4u);
             bulk_load(S.mass, o.mass + s_lo, len * 4u, &S.bar);
             bulk_load(S.com, o.com + 3 * s_lo, len * 12u, &S.bar);
             bulk_load(S.com_lo, o.com_lo + 3 * s_lo, len * 12u, &S.bar);
             bulk_load(S.quad, o.quad + 6 * s_lo, len * 24u, &S.bar);
             bulk_load(S.aabb, o.aabb + 6 * s_lo, len * 24u, &S.bar);
-        }
-        // while the copies fly: the parents whose first child is in the tile
-        // (a child is the first of its parent iff the parent differs from
-        // the previous cell's), listed in order
-        const int nt = (int)(c_hi - c_lo);
-        uint32_t before = 0;
-        for (int x0 = 0; x0 < nt; x0 += kLmThreads) {
-            const int x = x0 + (int)threadIdx.x;
-            int32_t p = -1;
-            bool first = false;
-            if (x < nt) {
-                const int64_t c = c_lo + x;
-                p = T.parent[c];
-                first = (c == off1) || T.parent[c - 1] != p;
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, first);
-            if (lane == 0) S.wcount[warp] = __popc(b);
-            __syncthreads();
-            uint32_t pre = before;
-            for (int w = 0; w < warp; ++w) pre += S.wcount[w];
-            if (first) S.own[pre + __popc(b & lanemask_lt())] = p;
-            for (int w = 0; w < kLmThreads / 32; ++w) before += S.wcount[w];
-            __syncthreads();
+            bulk_load(S.par, T.parent + p_lo, plen * 4u, &S.bar);
         }
         const bool ok = mbar_wait_bounded(&S.bar, phase, wait_limit);
         phase ^= 1u;
@@ -433,6 +419,38 @@ __global__ void __launch_bounds__(kLmThreads, 5)
             }
             return;
         }
+        // the parents whose first child is in the tile, in order: four
+        // children per thread, a warp prefix and one across the warps
+        const int nt = (int)(c_hi - c_lo);
+        uint32_t fl = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = 4 * (int)threadIdx.x + j;
+            if (x < nt) {
+                const int64_t c = c_lo + x;
+                if (c == off1 || S.par[c - p_lo] != S.par[c - 1 - p_lo]) fl |= 1u << j;
+            }
+        }
+        const uint32_t cnt = __popc(fl);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) S.wcount[warp] = incl;
+        __syncthreads();
+        uint32_t pos = incl - cnt, before = 0;
+#pragma unroll
+        for (int w = 0; w < kLmThreads / 32; ++w) {
+            const uint32_t v = S.wcount[w];
+            if (w < warp) pos += v;
+            before += v;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (fl & (1u << j)) S.own[pos++] = S.par[c_lo + 4 * (int)threadIdx.x + j - p_lo];
+        __syncthreads();
         const CellsStaged src{&S, s_lo};
         for (uint32_t i = threadIdx.x; i < before; i += kLmThreads)
             combine_children<MODE>(T, o, S.own[i], src);

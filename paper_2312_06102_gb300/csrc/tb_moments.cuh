@@ -458,7 +458,7 @@ __device__ __forceinline__ void child_offset(const Src &o, int64_t c, int a, flo
 }
 
 // Children [c0, c1) of p combined in FP64 (FP64 mode, or a cell of more
-// than 2^20 particles in the FP32 modes).  Kept out of line so that its
+// than 2^20 particles in the FP32-plain mode).  Kept out of line so that its
 // registers do not weigh on the FP32 path.
 template <int MODE>
 __device__ __noinline__ void combine_f64(const MomOut &o, int64_t p, int32_t c0, int32_t c1,
@@ -523,12 +523,13 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p, co
     };
     float bb[6];
     brow(c0, bb);
-    const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
     if constexpr (MODE == TB_MOM_FP32_COMP) {
-        if (!big) {
+        {
             // one pass: mass, first and second moments about the first
             // child's centre, then the shift to the centre of mass (as for a
-            // leaf)
+            // leaf).  The sums are compensated, and a parent's error is
+            // relative to its own mass and size whatever its particle count,
+            // so cells of any size take this route.
             float ref[3];
             for (int a = 0; a < 3; ++a) ref[a] = src.x(c0, a);
             AccS A;
@@ -552,6 +553,7 @@ __device__ void combine_children(const TreeIn &T, const MomOut &o, int64_t p, co
         brow(c, cb);
         grow(bb, cb);
     }
+    const bool big = (int64_t)(T.pend[p] - T.pfirst[p]) > kBigCell;
     if (MODE == TB_MOM_FP64 || big) {
         combine_f64<MODE>(o, p, c0, c1, bb);
     } else {
