@@ -96,9 +96,19 @@ __global__ void __launch_bounds__(kLcThreads, 3)
     const int nw = (int)((e - base + 3) / 4);
     uint64_t *key = reinterpret_cast<uint64_t *>(raw);
     uint32_t *cw = reinterpret_cast<uint32_t *>(raw + ((size_t)kLcTile + 4 * H + ncrit + 4) * 8);
-    for (int x = threadIdx.x; x < nk; x += kLcThreads) {
-        const int64_t i = base + x;
-        key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
+    // a block away from both ends of the array needs no bounds checks: every
+    // window [i, i + n] of its span exists and the keys load as 16-byte pairs
+    // (base is even, so key + base is 16-byte aligned)
+    const bool interior = base >= 0 && e == s + kLcTile && e + ncrit + 1 <= n;
+    if (interior) {
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(skeys + base);
+        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(key);
+        for (int x = threadIdx.x; 2 * x < nk; x += kLcThreads) dst[x] = src[x];
+    } else {
+        for (int x = threadIdx.x; x < nk; x += kLcThreads) {
+            const int64_t i = base + x;
+            key[x] = (i >= 0 && i < n) ? skeys[i] : 0ull;
+        }
     }
     for (int x = threadIdx.x; x < kLcSub * (kLevels + 1); x += kLcThreads) {
         (&hist_m[0][0])[x] = 0;
@@ -109,12 +119,20 @@ __global__ void __launch_bounds__(kLcThreads, 3)
     // window exists, else 0
     for (int w = threadIdx.x; w < nw; w += kLcThreads) {
         uint32_t v = 0;
+        if (interior) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = 4 * w + j;
-            const int64_t i = base + x;
-            if (i >= 0 && i + ncrit < n && i < e)
+            for (int j = 0; j < 4; ++j) {
+                const int x = 4 * w + j;
                 v |= (uint32_t)min(kDepthMax, min_depth(key[x], key[x + ncrit])) << (8 * j);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = 4 * w + j;
+                const int64_t i = base + x;
+                if (i >= 0 && i + ncrit < n && i < e)
+                    v |= (uint32_t)min(kDepthMax, min_depth(key[x], key[x + ncrit])) << (8 * j);
+            }
         }
         cw[w] = v;
     }
@@ -146,12 +164,18 @@ __global__ void __launch_bounds__(kLcThreads, 3)
         P = __vmaxu4(P, P << 16);
         Lw = __vmaxu4(__vmaxu4(S, P), I);
         mw = 0;
+        if (interior) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t k = k0 + j;
-            uint32_t m = 255u;
-            if (k < e) m = (k == 0) ? 0u : (uint32_t)min_depth(key[x0 + j - 1], key[x0 + j]);
-            mw |= m << (8 * j);
+            for (int j = 0; j < 4; ++j)
+                mw |= (uint32_t)min_depth(key[x0 + j - 1], key[x0 + j]) << (8 * j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t k = k0 + j;
+                uint32_t m = 255u;
+                if (k < e) m = (k == 0) ? 0u : (uint32_t)min_depth(key[x0 + j - 1], key[x0 + j]);
+                mw |= m << (8 * j);
+            }
         }
         // m and L of the four particles, for the emission
         if (k0 + 4 <= e) {
@@ -293,6 +317,7 @@ __global__ void __launch_bounds__(kScanThreads)
 // of their levels.
 constexpr int kEfThreads = 512;
 constexpr int kEfWarps = kEfThreads / 32;
+static_assert(kEfWarps <= 32, "one warp scans the warps' counts");
 constexpr int kEfTile = 2 * kLvTile;
 constexpr int kEfChunks = kEfTile / 32;
 
@@ -355,10 +380,17 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     }
     if (lane == 31) s_wcnt[warp] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t r = 0;
-        for (int w = 0; w < kEfWarps; ++w) { const uint32_t c = s_wcnt[w]; s_wcnt[w] = r; r += c; }
-        s_total = r;
+    if (warp == 0) {
+        // exclusive prefix of the warps' counts, by shuffles
+        const uint32_t c = lane < kEfWarps ? s_wcnt[lane] : 0u;
+        uint32_t r = c;
+#pragma unroll
+        for (int off = 1; off < kEfWarps; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, r, off);
+            if (lane >= off) r += y;
+        }
+        if (lane < kEfWarps) s_wcnt[lane] = r - c;
+        if (lane == kEfWarps - 1) s_total = r;
     }
     __syncthreads();
     uint32_t pos = s_wcnt[warp] + x - cnt;
