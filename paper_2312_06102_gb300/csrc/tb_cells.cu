@@ -404,6 +404,10 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __syncthreads();
     const int total = (int)s_total;
     const int nchunks = (total + 31) / 32;
+    // the keys of the warp's first chunk of starts, loaded now so that the
+    // mask and prefix phases below cover their latency
+    uint64_t Kfirst = 0;
+    if (warp * 32 + lane < total) Kfirst = skeys[s + (s_entry[warp * 32 + lane] & 2047u)];
     // level masks of every chunk of 32 starts (a 32 x 32 bit transpose)
     for (int c = warp; c < nchunks; c += kEfWarps) {
         const int i = c * 32 + lane;
@@ -423,11 +427,21 @@ __global__ void __launch_bounds__(kEfThreads, 2)
         if (lane < kLevels) s_mask[c][lane] = v;
     }
     __syncthreads();
-    if (threadIdx.x < kLevels) {
-        uint32_t r = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            s_cpre[c][threadIdx.x] = r;
-            r += __popc(s_mask[c][threadIdx.x]);
+    // per level, the starts in earlier chunks: a warp per level, a lane per
+    // chunk, 32 chunks at a time
+    for (int d = warp; d < kLevels; d += kEfWarps) {
+        uint32_t carry = 0;
+        for (int g = 0; g < nchunks; g += 32) {
+            const int c = g + lane;
+            const uint32_t v = c < nchunks ? (uint32_t)__popc(s_mask[c][d]) : 0u;
+            uint32_t r = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, r, off);
+                if (lane >= off) r += y;
+            }
+            if (c < nchunks) s_cpre[c][d] = carry + r - v;
+            carry += __shfl_sync(0xffffffffu, r, 31);
         }
     }
     __syncthreads();
@@ -439,7 +453,7 @@ __global__ void __launch_bounds__(kEfThreads, 2)
         const int64_t k = s + (en & 2047u);
         const int mm = (int)((en >> 11) & 31u), LL = (int)((en >> 16) & 31u), Lp = (int)((en >> 21) & 31u);
         auto P = [&](int d) { return s_base[d] + s_cpre[c][d] + (uint32_t)__popc(s_mask[c][d] & lt); };
-        const uint64_t K = skeys[k];
+        const uint64_t K = c == warp ? Kfirst : skeys[k];
         if (k > 0) {
             // close the cells holding k-1 but not k
             for (int d = mm; d <= Lp; ++d) {
