@@ -36,13 +36,13 @@ namespace tb {
 namespace {
 
 constexpr int kWalkWarps = 4;
-constexpr int kWalkBlocks = 152 * 8;
+constexpr int kWalkBlocks = 152 * 6;   // as many as fit (shared memory)
 constexpr int kWalkThreads = 32 * kWalkWarps;
 // cells waiting to be tested, per warp in global memory: a round takes at most
 // 32 cells and adds at most 7 per cell, and only cells above depth 21 have
 // children, so the stack stays below 21 * 256 + 1 entries
 constexpr int kStackCap = 6144;
-constexpr int kCellCap = 256;       // accepted cells
+constexpr int kCellCap = 128;       // accepted cells
 constexpr int kRangeCap = 128;      // particle ranges of opened leaves
 
 struct WalkTree {
@@ -56,7 +56,7 @@ struct WalkTree {
 };
 
 struct WarpLists {
-    int32_t cell[kCellCap];
+    float4 cell[kCellCap][4];       // the accepted cells' records, copied when accepted
     int2 range[kRangeCap];
 };
 
@@ -74,23 +74,24 @@ __device__ __forceinline__ float3 point_acc(float3 a, float rx, float ry, float 
 __device__ float3 evaluate(const WalkTree &T, const WarpLists &W, int ncell, int nrange, int64_t k,
                            int64_t ke, float eps2, bool use_quad, float3 a) {
     const float4 x = k < ke ? T.xs[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
     for (int j = 0; j < ncell; ++j) {
-        const int c = W.cell[j];
-        const float4 c0 = T.rec[4 * c], c1 = T.rec[4 * c + 1];
+        const float4 c0 = W.cell[j][0], c1 = W.cell[j][1];
         const float m = c0.w;
         const float rx = (x.x - c0.x) - c1.x;
         const float ry = (x.y - c0.y) - c1.y;
         const float rz = (x.z - c0.z) - c1.z;
         a = point_acc(a, rx, ry, rz, m, eps2);
         if (use_quad) {
-            const float4 t0 = T.rec[4 * c + 2], t1 = T.rec[4 * c + 3];
+            const float4 t0 = W.cell[j][2], t1 = W.cell[j][3];
             const float txx = t0.x, txy = t0.y, txz = t0.z, tyy = t0.w, tyz = t1.x, tzz = t1.y;
             const float trx = txx * rx + txy * ry + txz * rz;
             const float try_ = txy * rx + tyy * ry + tyz * rz;
             const float trz = txz * rx + tyz * ry + tzz * rz;
             const float rtr = rx * trx + ry * try_ + rz * trz;
-            const float ir2 = 1.f / (rx * rx + ry * ry + rz * rz);
-            const float ir5 = ir2 * ir2 * sqrtf(ir2);
+            const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+            const float ir2 = ir * ir;
+            const float ir5 = ir2 * ir2 * ir;
             const float s = 2.5f * rtr * ir5 * ir2;
             a.x += trx * ir5 - s * rx;
             a.y += try_ * ir5 - s * ry;
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kWalkThreads)
                 __syncwarp();
                 int kind = 0;                           // 1 accept, 2 leaf, 3 open
                 int nch = 0, c0 = 0;
+                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
                 if (c >= 0) {
                     const int32_t pf = T.pfirst[c], pe = T.pend[c];
                     const bool meets = pf < ke && kb < pe;
@@ -226,7 +228,8 @@ __global__ void __launch_bounds__(kWalkThreads)
                     bool accept = false;
                     if (!meets) {
                         const float l = scalbnf(side, -(int)T.level[c]);
-                        const float4 r0 = T.rec[4 * c], r1 = T.rec[4 * c + 1];
+                        r0 = T.rec[4 * c];
+                        r1 = T.rec[4 * c + 1];
                         const float cx[3] = {r0.x + r1.x, r0.y + r1.y, r0.z + r1.z};
                         float d2 = 0.f;
                         for (int a = 0; a < 3; ++a) {
@@ -241,7 +244,13 @@ __global__ void __launch_bounds__(kWalkThreads)
                 }
                 const unsigned ba = __ballot_sync(0xffffffffu, kind == 1);
                 const unsigned bl = __ballot_sync(0xffffffffu, kind == 2);
-                if (kind == 1) W.cell[ncell + __popc(ba & lt)] = c;
+                if (kind == 1) {
+                    float4 *dst = W.cell[ncell + __popc(ba & lt)];
+                    dst[0] = r0;
+                    dst[1] = r1;
+                    dst[2] = T.rec[4 * c + 2];
+                    dst[3] = T.rec[4 * c + 3];
+                }
                 if (kind == 2) W.range[nrange + __popc(bl & lt)] = make_int2(T.pfirst[c], T.pend[c]);
                 ncell += __popc(ba);
                 nrange += __popc(bl);
