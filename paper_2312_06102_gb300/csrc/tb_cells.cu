@@ -454,23 +454,31 @@ __global__ void __launch_bounds__(kEfThreads, 2)
         const int mm = (int)((en >> 11) & 31u), LL = (int)((en >> 16) & 31u), Lp = (int)((en >> 21) & 31u);
         auto P = [&](int d) { return s_base[d] + s_cpre[c][d] + (uint32_t)__popc(s_mask[c][d] & lt); };
         const uint64_t K = c == warp ? Kfirst : skeys[k];
+        // P(d) of consecutive levels: each loop computes one new level per step
+        const uint32_t pm = P(mm);
         if (k > 0) {
             // close the cells holding k-1 but not k
+            uint32_t pd = pm;
             for (int d = mm; d <= Lp; ++d) {
-                const uint32_t idx = P(d) - 1;
-                out.pend[idx] = (int32_t)k;
-                out.child_end[idx] = (d < Lp) ? (int32_t)P(d + 1) : -1;
+                const uint32_t pn = d < Lp ? P(d + 1) : 0u;
+                out.pend[pd - 1] = (int32_t)k;
+                out.child_end[pd - 1] = (d < Lp) ? (int32_t)pn : -1;
+                pd = pn;
             }
         }
-        for (int d = mm; d <= LL; ++d) {
-            const uint32_t idx = P(d);
-            out.ckey[idx] = cell_key(K, d);
-            out.level[idx] = (uint8_t)d;
-            out.pfirst[idx] = (int32_t)k;
-            out.parent[idx] = (d == 0) ? -1 : (int32_t)P(d - 1) - (d == mm ? 1 : 0);
-            out.child_first[idx] = (d < LL) ? (int32_t)P(d + 1) : -1;
+        uint32_t pprev = mm > 0 ? P(mm - 1) : 0u, pd = pm;
+        for (int d = mm;; ++d) {
+            const uint32_t pn = d < LL ? P(d + 1) : 0u;
+            out.ckey[pd] = cell_key(K, d);
+            out.level[pd] = (uint8_t)d;
+            out.pfirst[pd] = (int32_t)k;
+            out.parent[pd] = (d == 0) ? -1 : (int32_t)pprev - (d == mm ? 1 : 0);
+            out.child_first[pd] = (d < LL) ? (int32_t)pn : -1;
+            if (d == LL) break;
+            pprev = pd;
+            pd = pn;
         }
-        out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)P(LL);
+        out.leaf_cell[s_base[kLevels] + (uint32_t)i] = (int32_t)pd;
     }
 }
 
