@@ -306,22 +306,24 @@ __global__ void __launch_bounds__(kScanThreads)
     info->misc_ctr[1] = 0;
 }
 
-// Emission over the leaf starts only, two count tiles (2048 particles) per
-// block.  Only a leaf start (m_k <= L_k) opens or closes cells, about one
-// particle in seven, so the block first lists them in order in shared memory
+// Emission over the leaf starts only, one count tile (1024 particles) per
+// block of 256 threads, four blocks per SM.  Only a leaf start (m_k <= L_k)
+// opens or closes cells, one particle in four to seven on the tree
+// workloads, so the block first lists them in order in shared memory
 // (four particles per thread, a block-wide prefix of the counts) and then
 // runs the per-level prefix and the writes over that list, 32 starts per
 // warp: every lane holds a start, and the level masks are built for the
 // list, not for every particle.  The tree's last particle, which closes every
 // cell that holds it, is handled by its own thread: those are the last cells
 // of their levels.
-constexpr int kEfThreads = 512;
+constexpr int kEfThreads = 256;
 constexpr int kEfWarps = kEfThreads / 32;
 static_assert(kEfWarps <= 32, "one warp scans the warps' counts");
-constexpr int kEfTile = 2 * kLvTile;
+constexpr int kEfTile = 4 * kEfThreads;                // four particles per thread
+static_assert(kEfTile % kLvTile == 0 && kEfTile <= 2048, "whole count tiles; offsets fit 11 bits");
 constexpr int kEfChunks = kEfTile / 32;
 
-__global__ void __launch_bounds__(kEfThreads, 2)
+__global__ void __launch_bounds__(kEfThreads, 4)
     emit_starts_kernel(const uint64_t *__restrict__ skeys, const uint16_t *__restrict__ ml, int64_t n,
                        const uint32_t *__restrict__ tile_off, int64_t n_tiles, DevInfo *info_w,
                        EmitOut out) {
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kEfThreads, 2)
     __shared__ uint8_t s_Llast[kEfThreads];
     __shared__ uint32_t s_total;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t0 = 2 * (int64_t)blockIdx.x;          // first count tile of the block
+    const int64_t t0 = (int64_t)blockIdx.x * (kEfTile / kLvTile);   // first count tile of the block
     const int64_t s = (int64_t)blockIdx.x * kEfTile, e = min64(n, s + kEfTile);
     if (threadIdx.x < kLevelFields)
         s_base[threadIdx.x] = ((threadIdx.x < kLevels) ? (uint32_t)info->level_offset[threadIdx.x] : 0u) +
