@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kLvThreads, 2)
 }
 
 // The same counts, four consecutive particles per thread, for n_crit in
-// [kLcMinN, kLcMaxN].  A block takes two count tiles.  c is kept one byte per
+// [kLcMinN, kLcMaxN].  A block of 256 threads takes one count tile.  c is kept one byte per
 // position; the window maxima of four neighbours share all but their ends:
 // L_{k0+j} = max(suffix max from byte j of c[k0-n .. k0-n+3],
 //                max of c[k0-n+4 .. k0-1],
@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(kLvThreads, 2)
 // taken four bytes at a time (byte-wise SIMD maxima).  The per-level counts
 // come from histograms of m and of L + 1 over the leaf starts:
 // #cells started at level d = #{m <= d} - #{L + 1 <= d}.
-constexpr int kLcThreads = 512;
+constexpr int kLcThreads = 256;
 constexpr int kLcPer = 4;
-constexpr int kLcSub = 2;                               // count tiles per block
+constexpr int kLcSub = 1;                               // count tiles per block
 constexpr int kLcTile = kLvTile * kLcSub;
 constexpr int kLcMinN = 3, kLcMaxN = 60;
 
@@ -82,7 +82,7 @@ __host__ __device__ inline size_t lc_smem_bytes(int ncrit) {
     return nk * 8 + nw * 4;
 }
 
-__global__ void __launch_bounds__(kLcThreads, 3)
+__global__ void __launch_bounds__(kLcThreads, 6)
     level_count_fast_kernel(const uint64_t *__restrict__ skeys, int64_t n, int ncrit,
                             uint32_t *__restrict__ tile_cnt, int64_t n_tiles,
                             uint16_t *__restrict__ ml) {
