@@ -27,21 +27,26 @@ __device__ __forceinline__ uint64_t cell_key(uint64_t key, int d) {
     return key >> (63 - 3 * d);
 }
 
-// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
-__device__ __forceinline__ uint64_t spread3(uint32_t v) {
-    uint64_t x = v & 0x1fffffu;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
+// Spread bits 0..9 of v to every third bit (bit b -> bit 3b), in 32-bit
+// words.
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
 }
 
 // Key: a leading 1, then the 21 octant digits, x the most significant bit
-// of each digit (Sec. 2.2).
+// of each digit (Sec. 2.2).  Interleaved in 32-bit pieces: key bits 0..29
+// from coordinate bits 0..9, bits 30..59 from bits 10..19, 60..62 from bit 20.
 __device__ __forceinline__ uint64_t morton_key(uint32_t qx, uint32_t qy, uint32_t qz) {
-    return (1ull << 63) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    const uint32_t lo = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+    const uint32_t hx = qx >> 10, hy = qy >> 10, hz = qz >> 10;
+    const uint32_t hi = (spread10(hx) << 2) | (spread10(hy) << 1) | spread10(hz);
+    const uint32_t top = ((hx >> 10) << 2) | ((hy >> 10) << 1) | (hz >> 10);
+    return (1ull << 63) | ((uint64_t)top << 60) | ((uint64_t)hi << 30) | lo;
 }
 
 // Peano-Hilbert key (the alternative order of the footnote in Sec. 2.2):
