@@ -179,7 +179,7 @@ __device__ void front_sets(const BatchArgs &A, unsigned char *raw) {
     __shared__ uint32_t s_bad, s_tot[kLevelFields], s_tile[kLevelFields];
     __shared__ float s_lo[3], s_shi, s_slo;
     __shared__ double s_scale;
-    __shared__ bool s_exact;
+    __shared__ bool s_exact, s_f32;
     __shared__ int s_q;
     __shared__ int s_nlong;
     __shared__ int64_t s_long[32];
@@ -213,6 +213,7 @@ __device__ void front_sets(const BatchArgs &A, unsigned char *raw) {
             s_shi = (float)scale;
             s_slo = (float)__dsub_rn(scale, (double)s_shi);
             s_exact = !(scale < 1e30 && scale > 1e-30 && amax < 1e30f);
+            s_f32 = (double)s_shi == scale;
             for (int a = 0; a < 3; ++a) A.set_root[4 * (int64_t)set + a] = (double)s_lo[a];
             A.set_root[4 * (int64_t)set + 3] = L;
             if (s_bad) atomicOr(&A.info->status, kErrNonFinite);
@@ -223,15 +224,15 @@ __device__ void front_sets(const BatchArgs &A, unsigned char *raw) {
         {
             const float lx = s_lo[0], ly = s_lo[1], lz = s_lo[2], shi = s_shi, slo = s_slo;
             const double sc = s_scale;
-            const bool ex = s_exact;
+            const bool ex = s_exact, f32 = s_f32;
             const float m_eq = (float)(1.0 / (double)ns);
             // unsorted keys go where pass 0 reads them: kBPasses is odd, so the
             // passes run kalt -> pkey -> ... -> pkey
             for (int64_t i = o + threadIdx.x; i < o + ns; i += blockDim.x) {
                 const float x = A.pos[3 * i], y = A.pos[3 * i + 1], z = A.pos[3 * i + 2];
-                const uint64_t k = morton_key(quantise(x, lx, shi, slo, sc, ex),
-                                              quantise(y, ly, shi, slo, sc, ex),
-                                              quantise(z, lz, shi, slo, sc, ex));
+                const uint64_t k = morton_key(quantise(x, lx, shi, slo, sc, ex, f32),
+                                              quantise(y, ly, shi, slo, sc, ex, f32),
+                                              quantise(z, lz, shi, slo, sc, ex, f32));
                 A.kalt[i] = k;
                 A.xm[i] = make_float4(x, y, z, A.mass ? A.mass[i] : m_eq);
                 for (int p = 0; p < kBPasses; ++p)

@@ -40,7 +40,7 @@ struct DevInfo {
     uint32_t epoch;        // look-back epoch base of the current tree build
     uint32_t n_leaves;
     int32_t max_depth;
-    int32_t pad;
+    uint32_t s_fp32;       // 1: the scale is an FP32 value (scale == s_hi exactly)
     int64_t n_cells;
     int64_t level_offset[kLevels + 1];
     uint32_t sort_tile_ctr[16];   // dynamic tile ids, one counter per sort pass

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
         // the FP32 route needs x - lo and its products to stay far from overflow
         // and underflow; otherwise every coordinate takes the FP64 route
         info->exact_only = !(scale < 1e30 && scale > 1e-30 && amax < 1e30f) ? 1u : 0u;
+        info->s_fp32 = (double)s_hi == scale ? 1u : 0u;
         info->status = bad ? kErrNonFinite : 0u;
         info->epoch = (info->epoch + 16u) & 0x3fffffffu;
         for (int p = 0; p < 16; ++p) info->sort_tile_ctr[p] = 0;
@@ -183,27 +184,29 @@ __global__ void __launch_bounds__(kKeysThreads, 6) keys_kernel(const float *__re
     __shared__ float s_lo[3];
     __shared__ float s_shi, s_slo;
     __shared__ double s_scale;
-    __shared__ bool s_exact, s_last;
+    __shared__ bool s_exact, s_f32, s_last;
     if (threadIdx.x == 0) {
         for (int a = 0; a < 3; ++a) s_lo[a] = info->lo[a];
         s_shi = info->s_hi;
         s_slo = info->s_lo;
         s_scale = info->scale;
         s_exact = info->exact_only != 0;
+        s_f32 = info->s_fp32 != 0;
     }
     __syncthreads();
     const float lx = s_lo[0], ly = s_lo[1], lz = s_lo[2];
     const float shi = s_shi, slo = s_slo;
     const double sc = s_scale;
-    const bool exact = s_exact;
+    const bool exact = s_exact, f32 = s_f32;
 
     auto count = [&](uint64_t k) {
         for (int p = 0; p < passes; ++p)
             atomicAdd(&s_hist[p * RADIX + (int)((k >> (shift0 + p * RADIX_BITS)) & (RADIX - 1))], 1u);
     };
     auto key_of = [&](float x, float y, float z) {
-        const uint32_t qx = quantise(x, lx, shi, slo, sc, exact), qy = quantise(y, ly, shi, slo, sc, exact),
-                       qz = quantise(z, lz, shi, slo, sc, exact);
+        const uint32_t qx = quantise(x, lx, shi, slo, sc, exact, f32),
+                       qy = quantise(y, ly, shi, slo, sc, exact, f32),
+                       qz = quantise(z, lz, shi, slo, sc, exact, f32);
         return HILBERT ? hilbert_key(qx, qy, qz) : morton_key(qx, qy, qz);
     };
 
