@@ -19,8 +19,6 @@ struct RunSmem {
     // whose upper bits differ from every key's (keys leave bit 63 clear)
     __align__(16) uint64_t sk[kRunSpan + 4];
     uint32_t smask[kRunChunks];   // bit l of chunk c: position 32 c + l starts a run
-    int16_t prv[kRunChunks];      // last chunk <= c holding a start, or -1
-    int16_t nxt[kRunChunks];      // first chunk >= c holding a start
 };
 
 // Orders in place, by (low shift0 bits, position), every run of equal
@@ -35,7 +33,6 @@ __device__ bool run_tile(uint64_t *__restrict__ keys, int32_t *__restrict__ vals
     constexpr int PER = kRunTile / THREADS;
     uint64_t *sk = S.sk;
     uint32_t *smask = S.smask;
-    int16_t *prv = S.prv, *nxt = S.nxt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int te = (int)min64(kRunTile, hi - s);
     const int nw = (int)min64(kRunSpan, hi - s);
@@ -63,32 +60,8 @@ __device__ bool run_tile(uint64_t *__restrict__ keys, int32_t *__restrict__ vals
         if (lane == 0) smask[c] = m;
         multi |= (m != 0xffffffffu) && c * 32 <= te;   // includes position te (a run from te - 1)
     }
-    // a tile of single-key runs is done
+    // a tile of single-key runs is done (the barrier also publishes the masks)
     if (!__syncthreads_or(multi)) return false;
-    if (warp == 0) {
-        // prv / nxt over the chunks, 32 at a time with ballots
-        int carry = -1;
-        for (int g = 0; g < kRunChunks; g += 32) {
-            const int c = g + lane;
-            const bool has = c < kRunChunks && smask[c] != 0;
-            const uint32_t hm = __ballot_sync(0xffffffffu, has);
-            const uint32_t le = hm & (0xffffffffu >> (31 - lane));
-            const int p = le ? g + 31 - __clz(le) : carry;
-            if (c < kRunChunks) prv[c] = (int16_t)p;
-            carry = __shfl_sync(0xffffffffu, p, 31);
-        }
-        carry = kRunChunks - 1;   // the last chunk lies past the loaded span: all starts
-        for (int g = ((kRunChunks - 1) / 32) * 32; g >= 0; g -= 32) {
-            const int c = g + lane;
-            const bool has = c < kRunChunks && smask[c] != 0;
-            const uint32_t hm = __ballot_sync(0xffffffffu, has);
-            const uint32_t ge = hm & (0xffffffffu << lane);
-            const int q = ge ? g + __ffs(ge) - 1 : carry;
-            if (c < kRunChunks) nxt[c] = (int16_t)q;
-            carry = __shfl_sync(0xffffffffu, q, 0);
-        }
-    }
-    __syncthreads();
     // a run crossing the tile's end: its members past the end move too
     const bool crossing = te == kRunTile && nw > te && !((smask[te >> 5] >> (te & 31)) & 1u);
     int32_t dst[PER + 1];   // new position - s of the key at position x, or -1
@@ -106,29 +79,43 @@ __device__ bool run_tile(uint64_t *__restrict__ keys, int32_t *__restrict__ vals
         if (st_here && st_next) continue;               // a run of one key
         const uint64_t kx = sk[x + 2];
         if (!st_here) desc |= (kx & lowm) < (sk[x + 1] & lowm);
-        // the run [a, b) from the start masks
-        int a;
+        // the run [a, b) from the start masks, looking at most kScan chunks
+        // away: a run that reaches further is longer than kRunMax, and the
+        // member at its start queues it
+        constexpr int kScan = kRunMax / 32 + 2;
+        int a = -1;
         const uint32_t le = m & (0xffffffffu >> (31 - l));
         if (le) {
             a = c * 32 + 31 - __clz(le);
         } else {
-            const int pc = c > 0 ? prv[c - 1] : -1;
-            if (pc < 0) continue;                       // the run began before this tile
-            a = pc * 32 + 31 - __clz(smask[pc]);
+            for (int cc = c - 1; cc >= 0 && cc >= c - kScan; --cc) {
+                const uint32_t mc = smask[cc];
+                if (mc) {
+                    a = cc * 32 + 31 - __clz(mc);
+                    break;
+                }
+            }
+            if (a < 0) continue;                        // began before this tile, or long
         }
         if (a >= te) continue;                          // the run begins after this tile
         const uint32_t gt = l < 31 ? (m & (0xffffffffu << (l + 1))) : 0u;
-        int b;
+        int b = -1;                                     // stays -1 for a long run
         if (gt) {
             b = c * 32 + __ffs(gt) - 1;
         } else {
-            const int nc = nxt[c + 1];
-            b = nc * 32 + __ffs(smask[nc]) - 1;
+            // the chunk holding position nw starts runs from there on
+            for (int cc = c + 1; cc < kRunChunks && cc <= c + kScan; ++cc) {
+                const uint32_t mc = smask[cc];
+                if (mc) {
+                    b = cc * 32 + __ffs(mc) - 1;
+                    break;
+                }
+            }
         }
         if (b > nw) b = nw;
         // longer runs (including any that reach the end of the loaded span
         // before the end of the keys) go to the block sort
-        if (b - a > kRunMax) {
+        if (b < 0 || b - a > kRunMax) {
             if (x == a) queue_long(s + a);
             continue;
         }
