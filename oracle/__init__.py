@@ -52,6 +52,12 @@ def lib():
         L.ora_quantise.restype = C.c_uint32
         L.ora_root.argtypes = [vp, i64, vp, vp]
         L.ora_root.restype = C.c_int
+        L.ora_root_mode.argtypes = [vp, i64, vp, vp, C.c_int]
+        L.ora_root_mode.restype = C.c_int
+        L.ora_keys_root.argtypes = [vp, i64, vp, vp, vp, C.c_int, C.c_int]
+        L.ora_keys_root.restype = C.c_int
+        L.ora_build_root.argtypes = [vp, i64, i32, C.c_int, C.c_int]
+        L.ora_build_root.restype = vp
         L.ora_keys.argtypes = [vp, i64, vp, vp, vp]
         L.ora_keys.restype = C.c_int
         L.ora_keys_ordered.argtypes = [vp, i64, vp, vp, vp, C.c_int]
@@ -112,15 +118,31 @@ def hilbert(qx: int, qy: int, qz: int) -> int:
     return int(lib().ora_hilbert(qx, qy, qz))
 
 
-def keys(pos, order: str = "morton"):
-    """(keys uint64[n], lo float64[3], side) of the tight root cell (Sec. 2.2),
-    in Morton or Peano-Hilbert order."""
+ROOTS = {"tight": 0, "pow2": 1}
+
+
+def root(pos, root_mode: str = "tight"):
+    """(lo float64[3], side) of the root cell: the tight bounding box, or
+    (pow2) its side forced to the smallest power of two >= the largest extent
+    (Sec. 2.2), the corner staying at the per-axis minimum."""
+    pos = _f32pos(pos)
+    lo = np.zeros(3)
+    side = np.zeros(1)
+    if lib().ora_root_mode(_p(pos), pos.shape[0], _p(lo), _p(side), ROOTS[root_mode]):
+        raise ValueError("non-finite coordinate")
+    return lo, float(side[0])
+
+
+def keys(pos, order: str = "morton", root_mode: str = "tight"):
+    """(keys uint64[n], lo float64[3], side) of the root cell (Sec. 2.2), in
+    Morton or Peano-Hilbert order."""
     pos = _f32pos(pos)
     n = pos.shape[0]
     out = np.empty(n, dtype=np.uint64)
     lo = np.zeros(3)
     side = np.zeros(1)
-    st = lib().ora_keys_ordered(_p(pos), n, _p(lo), _p(side), _p(out), ORDERS[order])
+    st = lib().ora_keys_root(_p(pos), n, _p(lo), _p(side), _p(out), ORDERS[order],
+                             ROOTS[root_mode])
     if st:
         raise ValueError("non-finite coordinate")
     return out, lo, float(side[0])
@@ -174,12 +196,12 @@ class _Handle:
             pass
 
 
-def build_tree(pos, n_crit: int, order: str = "morton") -> Tree:
+def build_tree(pos, n_crit: int, order: str = "morton", root_mode: str = "tight") -> Tree:
     """Top-down Barnes-Hut build (Sec. 2.1) over sorted keys; canonical order
-    (level, then key in the chosen order)."""
+    (level, then key in the chosen order); root cell as in root()."""
     pos = _f32pos(pos)
     n = pos.shape[0]
-    h = lib().ora_build_ordered(_p(pos), n, int(n_crit), ORDERS[order])
+    h = lib().ora_build_root(_p(pos), n, int(n_crit), ORDERS[order], ROOTS[root_mode])
     if lib().ora_status(h):
         lib().ora_free(h)
         raise ValueError("non-finite coordinate")

@@ -30,7 +30,10 @@
  * Readings where the paper is silent (each one is also listed in the design
  * notes):
  *   - root cell: tight bounding box; corner lo = per-axis minimum, side
- *     L = largest per-axis extent (1 if all extents are 0).
+ *     L = largest per-axis extent (1 if all extents are 0).  With pow2 set,
+ *     the side is forced to the smallest power of two >= L (Sec. 2.2), the
+ *     corner staying at the minimum; keys taken from that corner are the
+ *     paper's keys about the root's centre shifted by 2^20 on every axis.
  *   - quantisation: q = min(2^21 - 1, floor((double(x) - double(lo)) * s)),
  *     s = 2^21 / L, every operation FP64 round-to-nearest, no contraction.
  *   - octant digit: (x bit << 2) | (y bit << 1) | (z bit), x most significant.
@@ -125,8 +128,18 @@ uint32_t ora_quantise(float x, double lo, double scale)
     return (uint32_t)f;
 }
 
-/* root cell: corner lo[3] and side; returns 0, or 1 if a coordinate is not finite */
-int ora_root(const float *pos, int64_t n, double lo[3], double *side)
+/* smallest power of two >= L, for L > 0 (exact: frexp gives L = m 2^e,
+ * m in [1/2, 1)) */
+static double pow2_ceil(double L)
+{
+    int e;
+    double m = frexp(L, &e);
+    return (m == 0.5) ? L : ldexp(1.0, e);
+}
+
+/* root cell: corner lo[3] and side; returns 0, or 1 if a coordinate is not
+ * finite.  pow2: side forced to a power of two (Sec. 2.2). */
+int ora_root_mode(const float *pos, int64_t n, double lo[3], double *side, int pow2)
 {
     double hi[3];
     for (int a = 0; a < 3; ++a) { lo[a] = 0.0; hi[a] = 0.0; }
@@ -145,15 +158,21 @@ int ora_root(const float *pos, int64_t n, double lo[3], double *side)
         double e = hi[a] - lo[a];
         if (e > L) L = e;
     }
-    *side = (L > 0.0) ? L : 1.0;
+    *side = (L > 0.0) ? (pow2 ? pow2_ceil(L) : L) : 1.0;
     return 0;
 }
 
-/* keys in Morton order (order 0) or Peano-Hilbert order (order 1) */
-int ora_keys_ordered(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys,
-                     int order)
+int ora_root(const float *pos, int64_t n, double lo[3], double *side)
 {
-    if (ora_root(pos, n, lo, side)) return 1;
+    return ora_root_mode(pos, n, lo, side, 0);
+}
+
+/* keys in Morton order (order 0) or Peano-Hilbert order (order 1), from the
+ * tight root cell or (pow2) the power-of-two one */
+int ora_keys_root(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys,
+                  int order, int pow2)
+{
+    if (ora_root_mode(pos, n, lo, side, pow2)) return 1;
     double scale = 2097152.0 / *side;
     for (int64_t i = 0; i < n; ++i) {
         uint32_t q[3];
@@ -161,6 +180,12 @@ int ora_keys_ordered(const float *pos, int64_t n, double lo[3], double *side, ui
         keys[i] = order ? ora_hilbert(q[0], q[1], q[2]) : ora_interleave(q[0], q[1], q[2]);
     }
     return 0;
+}
+
+int ora_keys_ordered(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys,
+                     int order)
+{
+    return ora_keys_root(pos, n, lo, side, keys, order, 0);
 }
 
 int ora_keys(const float *pos, int64_t n, double lo[3], double *side, uint64_t *keys)
@@ -264,7 +289,7 @@ static int idx_cmp(const void *pa, const void *pb)
     return 0;
 }
 
-ora_tree *ora_build_ordered(const float *pos, int64_t n, int32_t n_crit, int key_order)
+ora_tree *ora_build_root(const float *pos, int64_t n, int32_t n_crit, int key_order, int pow2)
 {
     ora_tree *t = (ora_tree *)calloc(1, sizeof(ora_tree));
     t->n = n;
@@ -273,7 +298,7 @@ ora_tree *ora_build_ordered(const float *pos, int64_t n, int32_t n_crit, int key
     uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * nn);
     t->skeys = (uint64_t *)malloc(sizeof(uint64_t) * nn);
     t->perm = (int32_t *)malloc(sizeof(int32_t) * nn);
-    t->status = ora_keys_ordered(pos, n, t->lo, &t->side, keys, key_order);
+    t->status = ora_keys_root(pos, n, t->lo, &t->side, keys, key_order, pow2);
     ora_sort(keys, n, t->skeys, t->perm);
     free(keys);
 
@@ -324,6 +349,11 @@ ora_tree *ora_build_ordered(const float *pos, int64_t n, int32_t n_crit, int key
     free(rank);
     free(cv.v);
     return t;
+}
+
+ora_tree *ora_build_ordered(const float *pos, int64_t n, int32_t n_crit, int key_order)
+{
+    return ora_build_root(pos, n, n_crit, key_order, 0);
 }
 
 ora_tree *ora_build(const float *pos, int64_t n, int32_t n_crit)

@@ -107,6 +107,63 @@ def test_keys_root_is_tight_box():
     assert q == (1 << 21) - 1
 
 
+@pytest.mark.parametrize("ext,want", [(3.0, 4.0), (4.0, 4.0), (0.125, 0.125), (0.3, 0.5),
+                                      (1e-3, 2.0 ** -9), (5000.0, 8192.0), (0.0, 1.0)])
+def test_root_pow2_side(ext, want):
+    """The power-of-two root (Sec. 2.2): the side is the smallest power of two
+    at least the largest extent (1 for a single point); the corner stays at
+    the per-axis minimum, and the tight root keeps the extent itself."""
+    e32 = float(np.float32(ext))
+    pos = np.array([[0.0, 0.0, 0.0], [e32, e32 / 2, 0.0], [e32 / 4, e32, e32 / 8]], np.float32)
+    lo, side = oracle.root(pos, "pow2")
+    assert np.array_equal(lo, [0.0, 0.0, 0.0])
+    assert side == want
+    lo_t, side_t = oracle.root(pos, "tight")
+    assert side_t == (e32 if e32 > 0 else 1.0)
+
+
+def test_keys_pow2_root_hand_point():
+    """With extent 3 the power-of-two side is 4 and the scale 2^19 exactly:
+    (3, 1.5, 0.75) quantises to (3, 1.5, 0.75) * 2^19, and its key, built here
+    bit by bit, has the octant digits 4, 6, 3, 1, 0, ... (the tight root, side
+    3, starts with 6 instead)."""
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 1.5, 0.75]], np.float32)
+    q = (3 * 2 ** 19, 3 * 2 ** 18, 3 * 2 ** 17)
+    want = 1
+    for b in range(20, -1, -1):
+        want = (want << 3) | (((q[0] >> b) & 1) << 2) | (((q[1] >> b) & 1) << 1) | ((q[2] >> b) & 1)
+    k, lo, side = oracle.keys(pos, root_mode="pow2")
+    assert side == 4.0 and int(k[1]) == want and int(k[0]) == 1 << 63
+    assert [(want >> (60 - 3 * j)) & 7 for j in range(5)] == [4, 6, 3, 1, 0]
+    kt, _, side_t = oracle.keys(pos)
+    assert side_t == 3.0 and (int(kt[1]) >> 60) & 7 == 6
+
+
+def test_tree_pow2_root_cell_boxes():
+    """Under the power-of-two root every cell of level d is the cube of side
+    side / 2^d at the integer corner its key spells out (x, y, z bits of each
+    octant digit), and holds exactly its members: each member lies in it."""
+    pos, _ = clustered_halos(6000, 9, n_halo=40)
+    t = oracle.build_tree(pos, 8, root_mode="pow2")
+    _check_invariants(t)
+    assert math.log2(t.side) == int(math.log2(t.side))
+    p = pos.astype(np.float64)[t.perm]
+    for c in range(t.n_cells):
+        d = int(t.level[c])
+        key = int(t.ckey[c])
+        ijk = [0, 0, 0]
+        for j in range(d):
+            dig = (key >> (3 * (d - 1 - j))) & 7
+            for a in range(3):
+                ijk[a] = (ijk[a] << 1) | ((dig >> (2 - a)) & 1)
+        h = t.side / 2 ** d
+        mem = p[t.pfirst[c]:t.pend[c]]
+        for a in range(3):
+            lo_c = t.lo[a] + ijk[a] * h
+            assert np.all(mem[:, a] >= lo_c - 1e-12 * t.side)
+            assert np.all(mem[:, a] <= lo_c + h + 1e-12 * t.side)
+
+
 def test_keys_monotone_per_axis():
     """Moving one coordinate up never lowers that axis's quantised value
     (read back from the key by de-interleaving)."""
