@@ -108,6 +108,11 @@ typedef struct {
                                 whole build as one cooperative launch (phases separated
                                 by grid barriers); 0 (default) runs it as separate
                                 launches, which measured faster */
+    int32_t root_pow2;       /* 0 (default): the root cube's side is the largest extent
+                                of the particles' bounding box; 1: it is forced to the
+                                smallest power of two at least that extent (Sec. 2.2),
+                                the corner staying at the per-axis minimum (tb_build
+                                and, per set, tb_build_batched) */
 } tb_params;
 
 /* Host-side description of a tree.  Scalars are valid after a build with

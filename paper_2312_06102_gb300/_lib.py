@@ -27,7 +27,7 @@ class Params(C.Structure):
     _fields_ = [("n_crit", C.c_int32), ("mom_mode", C.c_int32), ("cell_capacity", C.c_int64),
                 ("reorder", C.c_int32), ("radix_bits", C.c_int32), ("sort_threads", C.c_int32),
                 ("sort_items", C.c_int32), ("batch_threads", C.c_int32), ("key_order", C.c_int32),
-                ("batch_one_launch", C.c_int32)]
+                ("batch_one_launch", C.c_int32), ("root_pow2", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -256,10 +256,11 @@ KEYS_MORTON, KEYS_HILBERT = 0, 1
 def build(pos: torch.Tensor, mass: torch.Tensor | None = None, n_crit: int = 16,
           mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0, reorder: bool = False,
           radix_bits: int = 0, tree: Tree | None = None, stream=None, sort_cfg=None,
-          key_order: int = KEYS_MORTON) -> Tree:
+          key_order: int = KEYS_MORTON, root_pow2: bool = False) -> Tree:
     """tb_build on a [n,3] float32 CUDA tensor; returns (or rebuilds) a Tree.
     sort_cfg = (radix_bits, threads, items) picks a compiled sort variant;
-    key_order is KEYS_MORTON or KEYS_HILBERT."""
+    key_order is KEYS_MORTON or KEYS_HILBERT; root_pow2 forces the root
+    cube's side to a power of two."""
     if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3:
         raise ValueError("pos must be a [n,3] float32 tensor")
     t = tree if tree is not None else Tree()
@@ -268,6 +269,7 @@ def build(pos: torch.Tensor, mass: torch.Tensor | None = None, n_crit: int = 16,
         sort_cfg = autotune.cached(pos.shape[0])
     p = _params(n_crit, mom_mode, cell_capacity, reorder, radix_bits, 0, sort_cfg)
     p.key_order = int(key_order)
+    p.root_pow2 = int(bool(root_pow2))
     code = lib().tb_build(_ptr(pos), _ptr(mass), pos.shape[0], C.byref(p), _stream(stream),
                           C.byref(t._p))
     _check(code, "tb_build")
@@ -284,7 +286,7 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
                   n_crit: int = 16, mom_mode: int = MOM_FP32_COMP, cell_capacity: int = 0,
                   radix_bits: int = 0, batch_threads: int = 0, tree: Tree | None = None,
                   n_total: int | None = None, stream=None, key_order: int = KEYS_MORTON,
-                  one_launch: bool = False) -> Tree:
+                  one_launch: bool = False, root_pow2: bool = False) -> Tree:
     """tb_build_batched: set s holds pos[set_offsets[s]:set_offsets[s+1]];
     one_launch (with cell_capacity > 0) runs it as one cooperative launch."""
     if set_offsets.dtype != torch.int64 or not set_offsets.is_cuda:
@@ -297,6 +299,7 @@ def build_batched(pos: torch.Tensor, mass: torch.Tensor | None, set_offsets: tor
     p = _params(n_crit, mom_mode, cell_capacity, 0, radix_bits, batch_threads)
     p.key_order = int(key_order)
     p.batch_one_launch = int(bool(one_launch))
+    p.root_pow2 = int(bool(root_pow2))
     n_total = pos.shape[0] if n_total is None else n_total
     code = lib().tb_build_batched(_ptr(pos), _ptr(mass), _ptr(set_offsets),
                                   set_offsets.shape[0] - 1, int(n_total), C.byref(p),

@@ -214,6 +214,7 @@ bool valid_params(const tb_params *p) {
            (p->key_order == TB_KEYS_MORTON || p->key_order == TB_KEYS_HILBERT) &&
            batch_threads_valid(p->batch_threads) &&
            (p->batch_one_launch == 0 || p->batch_one_launch == 1) &&
+           (p->root_pow2 == 0 || p->root_pow2 == 1) &&
            sort_cfg_valid(pick_cfg(p));
 }
 
@@ -318,6 +319,7 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
     }
     const int passes = sort_plan(cfg).passes;
     mark(ws, "start", s);
+    ws.root_pow2 = params->root_pow2 != 0;
     cudaError_t e = launch_root(d_pos, n, ws, passes << cfg.radix_bits, s);
     if (e != cudaSuccess) return from_cuda(e);
     mark(ws, "root", s);
@@ -443,6 +445,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
     tb_tree &t = S->pub;
     S->params = *params;
     ws.last_stream = s;
+    ws.root_pow2 = params->root_pow2 != 0;
     t.n_particles = n_total;
     t.n_crit = params->n_crit;
     t.n_sets = n_sets;

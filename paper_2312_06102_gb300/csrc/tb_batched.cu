@@ -65,6 +65,7 @@ struct BatchArgs {
     double *set_root;         // [S][4]
     uint32_t *queue;          // [8] work-queue tickets [0..2], grid barrier [4..5]
     DevInfo *info;
+    int32_t root_pow2;        // each set's root side forced to a power of two
 };
 
 template <int T>
@@ -208,6 +209,7 @@ __device__ void front_sets(const BatchArgs &A, unsigned char *raw) {
                 amax = fmaxf(amax, fmaxf(fabsf(s_red[a]), fabsf(s_red[3 + a])));
             }
             if (!(L > 0.0)) L = 1.0;
+            if (A.root_pow2) L = pow2_ceil(L);
             const double scale = __ddiv_rn(2097152.0, L);
             s_scale = scale;
             s_shi = (float)scale;
@@ -688,7 +690,7 @@ cudaError_t launch_batched_one(const float *pos, const float *mass, const int64_
                                int64_t cell_cap, int mode, cudaStream_t s) {
     BatchArgs A{pos, mass, off, ws.set_order, S, ncrit, t.pkey, t.perm, ws.keys_alt,
                 ws.perm_alt, ws.xm, ws.xs, ws.ml, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
-                t.set_root, ws.set_ctr, ws.info};
+                t.set_root, ws.set_ctr, ws.info, ws.root_pow2 ? 1 : 0};
     const int T = threads ? threads : kBDefaultThreads;
 #define TB_ONE(TT, MM) \
     if (T == TT && mode == MM) return launch_batched_one_t<TT, MM>(A, S, ncrit, n_total, t, ws, cell_cap, s);
@@ -707,7 +709,7 @@ cudaError_t launch_batched(const float *pos, const float *mass, const int64_t *o
                            int phase, int mode, cudaStream_t s) {
     BatchArgs A{pos, mass, off, ws.set_order, S, ncrit, t.pkey, t.perm, ws.keys_alt,
                 ws.perm_alt, ws.xm, ws.xs, ws.ml, ws.set_cnt, t.set_cell_offset, ws.set_leaf_off,
-                t.set_root, ws.set_ctr, ws.info};
+                t.set_root, ws.set_ctr, ws.info, ws.root_pow2 ? 1 : 0};
     switch (threads ? threads : kBDefaultThreads) {
         case 512: return launch_batched_t<512>(A, S, ncrit, t, ws, cell_cap, phase, mode, s);
         case 1024: return launch_batched_t<1024>(A, S, ncrit, t, ws, cell_cap, phase, mode, s);

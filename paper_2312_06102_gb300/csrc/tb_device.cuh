@@ -22,6 +22,14 @@ __device__ __forceinline__ int min_depth(uint64_t a, uint64_t b) {
     return (__clzll(a ^ b) + 2) / 3;
 }
 
+// The smallest power of two >= L, for L > 0 (the power-of-two root cube of
+// Sec. 2.2): L = m 2^e with m in [1/2, 1), exactly.
+__device__ __forceinline__ double pow2_ceil(double L) {
+    int e;
+    const double m = frexp(L, &e);
+    return m == 0.5 ? L : ldexp(1.0, e);
+}
+
 // Depth-d cell key of a particle key: its upper 3d+1 bits (Sec. 2.3.1).
 __device__ __forceinline__ uint64_t cell_key(uint64_t key, int d) {
     return key >> (63 - 3 * d);

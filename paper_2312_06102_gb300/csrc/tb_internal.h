@@ -76,6 +76,7 @@ struct Workspace {
     int64_t bbox_blocks = 0;
     int64_t cell_cap_request = 0;   // params.cell_capacity of the current build
     int64_t reorder_cap = 0;
+    bool root_pow2 = false;          // root side forced to a power of two (this build)
 
     float4 *xm = nullptr;            // [n] (x, y, z, m) in input order, written with the keys
     float4 *xs = nullptr;            // [n] the same records in key order (reorder only)

@@ -43,7 +43,7 @@ struct Box {
 __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restrict__ pos, int64_t n,
                                                             bool vec, float *__restrict__ part,
                                                             DevInfo *info, uint32_t *hist,
-                                                            int hist_len) {
+                                                            int hist_len, bool pow2) {
     Box b;
     b.init();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(const float *__restr
             amax = fmaxf(amax, fmaxf(fabsf(s_red[0][a]), fabsf(s_red[0][3 + a])));
         }
         if (!(L > 0.0)) L = 1.0;
+        if (pow2) L = pow2_ceil(L);
         double scale = __ddiv_rn(2097152.0, L);
         float s_hi = (float)scale;
         float s_lo = (float)__dsub_rn(scale, (double)s_hi);
@@ -289,7 +290,7 @@ cudaError_t launch_root(const float *pos, int64_t n, Workspace &ws, int hist_len
     int64_t need = (n + 4 * kRootThreads - 1) / (4 * kRootThreads);
     if (need < grid) grid = need < 1 ? 1 : need;
     root_kernel<<<(unsigned)grid, kRootThreads, 0, s>>>(pos, n, vec, ws.bbox_part, ws.info, ws.hist,
-                                                        hist_len);
+                                                        hist_len, ws.root_pow2);
     ++g_launches;
     return cudaGetLastError();
 }

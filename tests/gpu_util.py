@@ -26,12 +26,13 @@ def to_np(t):
 
 
 def gpu_tree(pos, mass, n_crit, mode=0, radix_bits=0, cell_capacity=0, moments=True,
-             reorder=False, key_order=0):
+             reorder=False, key_order=0, root_pow2=False):
     m = tb()
     p = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).cuda()
     w = None if mass is None else torch.from_numpy(np.ascontiguousarray(mass, np.float32)).cuda()
     t = m.build(p, w, n_crit=n_crit, mom_mode=mode, radix_bits=radix_bits,
-                cell_capacity=cell_capacity, reorder=reorder, key_order=key_order)
+                cell_capacity=cell_capacity, reorder=reorder, key_order=key_order,
+                root_pow2=root_pow2)
     if cell_capacity:
         st = t.sync()
         assert st == 0, m.STATUS[st]

@@ -40,8 +40,8 @@ def _build(tb, pos, mass, n, p):
 
 def test_defaults_are_valid_values(tb):
     p = _params(tb)
-    assert (p.n_crit, p.mom_mode, p.cell_capacity, p.reorder, p.radix_bits, p.key_order) == \
-        (16, 0, 0, 0, 0, 0)
+    assert (p.n_crit, p.mom_mode, p.cell_capacity, p.reorder, p.radix_bits, p.key_order,
+            p.root_pow2) == (16, 0, 0, 0, 0, 0, 0)
 
 
 def test_build_rejects_null_tree_and_params(tb):
@@ -61,6 +61,7 @@ def test_build_rejects_particle_counts(tb, n):
     ("cell_capacity", -1), ("cell_capacity", 1 << 31),   # cell indices are int32
     ("radix_bits", 7), ("radix_bits", 12),
     ("key_order", 2), ("key_order", -1),
+    ("root_pow2", 2), ("root_pow2", -1),
     ("sort_threads", 300), ("sort_items", 5),
 ])
 def test_build_rejects_params(tb, field, value):

@@ -12,19 +12,19 @@ pytestmark = pytest.mark.gpu
 from gpu_util import TOL_COM, TOL_MASS, TOL_QUAD, tb, to_np, torch  # noqa: E402
 
 
-def _run(pos, mass, offsets, n_crit=16, cap=0, mode=0, tree=None, threads=512):
+def _run(pos, mass, offsets, n_crit=16, cap=0, mode=0, tree=None, threads=512, root_pow2=False):
     m = tb()
     p = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).cuda()
     w = None if mass is None else torch.from_numpy(np.ascontiguousarray(mass, np.float32)).cuda()
     off = torch.from_numpy(np.asarray(offsets, np.int64)).cuda()
     t = m.build_batched(p, w, off, n_crit=n_crit, cell_capacity=cap, mom_mode=mode, tree=tree,
-                        batch_threads=threads)
+                        batch_threads=threads, root_pow2=root_pow2)
     torch.cuda.synchronize()
     assert t.sync() == 0
     return t, p, w, off
 
 
-def _check_sets(t, pos, mass, offsets, n_crit, sets=None, mode=0):
+def _check_sets(t, pos, mass, offsets, n_crit, sets=None, mode=0, root_mode="tight"):
     offsets = np.asarray(offsets, np.int64)
     S = len(offsets) - 1
     g = {k: to_np(getattr(t, k)) for k in ("pkey", "perm", "ckey", "level", "parent",
@@ -41,7 +41,7 @@ def _check_sets(t, pos, mass, offsets, n_crit, sets=None, mode=0):
             continue
         sp = pos[a:b]
         sm = None if mass is None else mass[a:b]
-        o = oracle.build_tree(sp, n_crit)
+        o = oracle.build_tree(sp, n_crit, root_mode=root_mode)
         assert c1 - c0 == o.n_cells, (s, c1 - c0, o.n_cells)
         assert np.array_equal(g["pkey"][a:b], o.skeys), s
         assert np.array_equal(g["perm"][a:b] - a, o.perm), s
@@ -169,6 +169,14 @@ def test_batched_graph_replay_with_jitter(one_launch):
         torch.cuda.synchronize()
         assert t.sync() == 0
         _check_sets(t, pj, b.mass, b.offsets, 16, sets=[0, 1, 17, 40, 63])
+
+
+def test_batched_root_pow2():
+    """Every set's root cube with its side forced to a power of two (Sec. 2.2)
+    equals the oracle's tree of that set under the same root."""
+    pos, mass, offsets = _sets([1, 7, 300, 4096, 0, 9000, 33], 61)
+    t, p, w, off = _run(pos, mass, offsets, root_pow2=True)
+    _check_sets(t, pos, mass, offsets, 16, root_mode="pow2")
 
 
 def test_batched_invalid_offsets_rejected():

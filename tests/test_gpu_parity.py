@@ -372,6 +372,27 @@ def test_moments_repeat_on_one_build(mode):
             assert np.array_equal(to_np(getattr(t, k)), v), k
 
 
+@pytest.mark.parametrize("gen,n_crit", [("plummer", 16), ("clustered", 8), ("stress", 16),
+                                         ("uniform", 1)])
+def test_root_pow2(gen, n_crit):
+    """The power-of-two root cube (Sec. 2.2): side forced to the smallest
+    power of two at least the extent; keys, cells and moments equal the
+    oracle's under the same root.  The scale is then a power of two, so
+    every ambiguous quantisation takes the exact FP32 route."""
+    pos, mass = {"plummer": lambda: plummer(1 << 16, 41),
+                 "clustered": lambda: clustered_halos(1 << 16, 42, n_halo=60),
+                 "stress": lambda: precision_stress(1 << 16, 43, n_halo=60),
+                 "uniform": lambda: uniform_cube(5000, 44)}[gen]()
+    o = oracle.build_tree(pos, n_crit, root_mode="pow2")
+    assert o.side == 2.0 ** np.ceil(np.log2(o.side))
+    t, p, w = gpu_tree(pos, mass, n_crit, root_pow2=True)
+    assert_structure_equal(t, o)
+    M, com, quad, aabb = oracle.moments(o, pos, mass)
+    em, ec, eq, bb_ok = moment_errors(t, o, M, com, quad, aabb)
+    assert bb_ok
+    assert em.max() <= TOL_MASS and ec.max() <= TOL_COM and eq.max() <= TOL_QUAD
+
+
 def test_bounded_wait_times_out():
     m = tb()
     assert m.STATUS[m.selftest_wait(1000)] == "TB_ETIMEOUT"
