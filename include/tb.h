@@ -236,7 +236,7 @@ tb_status tb_build_batched(const float *d_pos, const float *d_mass, const int64_
  *   n_group  group size bound, 1 <= n_group <= 2^20
  *   d_acc    [n_particles][3] FP32 out, device, caller-owned, in the
  *            caller's original particle order
- * Scratch (per-warp traversal stacks of about 30 MB, plus 68 B per cell for
+ * Scratch (per-warp traversal stacks of about 30 MB, plus 84 B per cell for
  * the group list and a packed copy of the moments) is allocated on first use
  * and kept with the tree.  A traversal stack
  * that fills (not expected for trees of depth <= 21) sets a device status that

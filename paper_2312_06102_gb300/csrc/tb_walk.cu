@@ -109,19 +109,30 @@ __device__ float3 evaluate(const WalkTree &T, const WarpLists &W, int ncell, int
     return a;
 }
 
-// Per cell, the four float4 the list evaluation reads: centre and mass, the
-// centre's low part, and the traceless tensor T = 3 Q - tr(Q) I.
+// Per cell, kRec float4: the four the list evaluation reads (centre and
+// mass; the centre's low part, with the cell's level in the last word; the
+// traceless tensor T = 3 Q - tr(Q) I) and the links the traversal reads
+// (pfirst, pend, child_first, child_end), so that a cell tested costs three
+// 16-byte loads.
+constexpr int kRec = 5;
+
 __global__ void walk_pack_kernel(const float *__restrict__ mass, const float *__restrict__ com,
                                  const float *__restrict__ com_lo, const float *__restrict__ quad,
-                                 int64_t n_cells, float4 *__restrict__ rec) {
+                                 const uint8_t *__restrict__ level, const int32_t *__restrict__ pfirst,
+                                 const int32_t *__restrict__ pend, const int32_t *__restrict__ child_first,
+                                 const int32_t *__restrict__ child_end, int64_t n_cells,
+                                 float4 *__restrict__ rec) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells; c += stride) {
         const float *q = quad + 6 * c;
         const float tr = q[0] + q[3] + q[5];
-        rec[4 * c] = make_float4(com[3 * c], com[3 * c + 1], com[3 * c + 2], mass[c]);
-        rec[4 * c + 1] = make_float4(com_lo[3 * c], com_lo[3 * c + 1], com_lo[3 * c + 2], 0.f);
-        rec[4 * c + 2] = make_float4(3.f * q[0] - tr, 3.f * q[1], 3.f * q[2], 3.f * q[3] - tr);
-        rec[4 * c + 3] = make_float4(3.f * q[4], 3.f * q[5] - tr, 0.f, 0.f);
+        float4 *r = rec + kRec * c;
+        r[0] = make_float4(com[3 * c], com[3 * c + 1], com[3 * c + 2], mass[c]);
+        r[1] = make_float4(com_lo[3 * c], com_lo[3 * c + 1], com_lo[3 * c + 2],
+                           __int_as_float((int)level[c]));
+        r[2] = make_float4(3.f * q[0] - tr, 3.f * q[1], 3.f * q[2], 3.f * q[3] - tr);
+        r[3] = make_float4(3.f * q[4], 3.f * q[5] - tr, 0.f, 0.f);
+        reinterpret_cast<int4 *>(r)[4] = make_int4(pfirst[c], pend[c], child_first[c], child_end[c]);
     }
 }
 
@@ -221,15 +232,16 @@ __global__ void __launch_bounds__(kWalkThreads)
                 int kind = 0;                           // 1 accept, 2 leaf, 3 open
                 int nch = 0, c0 = 0;
                 float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+                int4 lk = make_int4(0, 0, 0, 0);        // pfirst, pend, child_first, child_end
                 if (c >= 0) {
-                    const int32_t pf = T.pfirst[c], pe = T.pend[c];
-                    const bool meets = pf < ke && kb < pe;
-                    c0 = T.child_first[c];
+                    lk = reinterpret_cast<const int4 *>(T.rec + kRec * (int64_t)c)[4];
+                    const bool meets = lk.x < ke && kb < lk.y;
+                    c0 = lk.z;
                     bool accept = false;
                     if (!meets) {
-                        const float l = scalbnf(side, -(int)T.level[c]);
-                        r0 = T.rec[4 * c];
-                        r1 = T.rec[4 * c + 1];
+                        r0 = T.rec[kRec * (int64_t)c];
+                        r1 = T.rec[kRec * (int64_t)c + 1];
+                        const float l = scalbnf(side, -__float_as_int(r1.w));
                         const float cx[3] = {r0.x + r1.x, r0.y + r1.y, r0.z + r1.z};
                         float d2 = 0.f;
                         for (int a = 0; a < 3; ++a) {
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(kWalkThreads)
                     }
                     if (accept) kind = 1;
                     else if (c0 < 0) kind = 2;
-                    else { kind = 3; nch = T.child_end[c] - c0; }
+                    else { kind = 3; nch = lk.w - c0; }
                 }
                 const unsigned ba = __ballot_sync(0xffffffffu, kind == 1);
                 const unsigned bl = __ballot_sync(0xffffffffu, kind == 2);
@@ -248,10 +260,10 @@ __global__ void __launch_bounds__(kWalkThreads)
                     float4 *dst = W.cell[ncell + __popc(ba & lt)];
                     dst[0] = r0;
                     dst[1] = r1;
-                    dst[2] = T.rec[4 * c + 2];
-                    dst[3] = T.rec[4 * c + 3];
+                    dst[2] = T.rec[kRec * (int64_t)c + 2];
+                    dst[3] = T.rec[kRec * (int64_t)c + 3];
                 }
-                if (kind == 2) W.range[nrange + __popc(bl & lt)] = make_int2(T.pfirst[c], T.pend[c]);
+                if (kind == 2) W.range[nrange + __popc(bl & lt)] = make_int2(lk.x, lk.y);
                 ncell += __popc(ba);
                 nrange += __popc(bl);
                 // children onto the stack (exclusive scan of the counts)
@@ -287,15 +299,15 @@ __global__ void __launch_bounds__(kWalkThreads)
 }  // namespace
 
 int64_t walk_buffer_words(int64_t n_cells) {
-    return 16 * n_cells + 8 + n_cells + (int64_t)kWalkBlocks * kWalkWarps * kStackCap;
+    return 4 * kRec * n_cells + 8 + n_cells + (int64_t)kWalkBlocks * kWalkWarps * kStackCap;
 }
 
 cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps, int n_group,
                         int use_quad, float *acc, int32_t *buf, cudaStream_t s) {
     float4 *rec = reinterpret_cast<float4 *>(buf);   // first: 16-byte aligned
-    uint32_t *ctr = reinterpret_cast<uint32_t *>(buf + 16 * t.n_cells);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(buf + 4 * kRec * t.n_cells);
     ws.walk_ctr = ctr;
-    int32_t *groups = buf + 16 * t.n_cells + 8;
+    int32_t *groups = buf + 4 * kRec * t.n_cells + 8;
     int32_t *stacks = groups + t.n_cells;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
@@ -306,7 +318,9 @@ cudaError_t launch_walk(const tb_tree &t, Workspace &ws, float theta, float eps,
                                                       t.n_cells, n_group, groups, ctr);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    walk_pack_kernel<<<(unsigned)grid, 256, 0, s>>>(t.mass, t.com, t.com_lo, t.quad, t.n_cells, rec);
+    walk_pack_kernel<<<(unsigned)grid, 256, 0, s>>>(t.mass, t.com, t.com_lo, t.quad, t.level, t.pfirst,
+                                                    t.pend, t.child_first, t.child_end, t.n_cells,
+                                                    rec);
     ++g_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     WalkTree T{t.child_first, t.child_end, t.pfirst, t.pend, t.level, t.mass, t.com, t.com_lo,
