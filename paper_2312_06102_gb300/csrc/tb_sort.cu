@@ -143,9 +143,24 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? (ITEMS <= 8 ? 4 : 2
         }
         my_count[r] = acc;
     }
-    // exclusive scan of the counts over digits (each thread holds a
-    // contiguous group of digits when RADIX > THREADS)
-    {
+    // exclusive scan of the counts over digits
+    if constexpr (RADIX <= THREADS) {
+        // one digit per thread: a warp scan and one across the warps
+        const uint32_t c = (threadIdx.x < RADIX) ? my_count[0] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) sm.scan_tmp[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += sm.scan_tmp[w];
+        if (threadIdx.x < RADIX) sm.tile_off[threadIdx.x] = wpre + x - c;
+        if (threadIdx.x == 0) sm.tile_off[RADIX] = (uint32_t)valid;
+    } else {
+        // each thread holds a contiguous group of digits
         constexpr int PER = (RADIX + THREADS - 1) / THREADS;
         // regroup: thread t owns digits [t*PER, t*PER+PER) for the scan
         __syncthreads();
