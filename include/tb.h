@@ -191,13 +191,15 @@ tb_status tb_build(const float *d_pos, const float *d_mass, int64_t n, const tb_
  * stream has completed, the caller may refill those arrays, e.g. with the
  * next step's copy.  Other pointers are read afresh.  Leaves of more than
  * 2^20 particles are summed in FP64 in every mode (parents of that many in
- * the FP32-plain mode too).  Returns TB_EINVAL when the
+ * the FP32-plain mode too).  Calling it again on the same build gives the
+ * same moments bit for bit.  Returns TB_EINVAL when the
  * tree's last tb_build returned an error before it enqueued every stage. */
 tb_status tb_moments(tb_tree *tree, const float *d_pos, const float *d_mass, tb_stream stream);
 
 /* Build S independent trees in one call, moments included.  Particles of set
  * s are d_pos[d_set_offsets[s] .. d_set_offsets[s+1]); each set has its own
- * tight root cube.  Cells of each set are contiguous and canonical within the
+ * root cube (the tight one, or with root_pow2 its side forced to a power of
+ * two).  Cells of each set are contiguous and canonical within the
  * set; parent / child / particle indices are global (into the whole arrays).
  *   d_set_offsets  [S+1] int64, device, non-decreasing, d_set_offsets[0] = 0
  *   n_total        d_set_offsets[S] (the host must know it for allocation)
