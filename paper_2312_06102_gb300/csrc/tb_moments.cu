@@ -341,7 +341,9 @@ __global__ void __launch_bounds__(kMomThreads, 4)
 // differs from the previous cell's), and combines them there.  Each copy
 // covers whole groups of four cells, so that every array's piece starts on a
 // 16-byte boundary; the moment and parent arrays are allocated kMomentPad
-// cells past the capacity, which the rounding never passes.  Blocks loop
+// cells past the capacity, which the rounding never passes.  The up to three
+// cells the rounding adds before a level's first tile belong to level d,
+// which this launch writes: they are copied but never read.  Blocks loop
 // over the tiles of the level (one persistent grid per launch).
 constexpr int kLmThreads = 128;
 constexpr int kLmTile = 512;
