@@ -139,14 +139,17 @@ def test_keys_pow2_root_hand_point():
     assert side_t == 3.0 and (int(kt[1]) >> 60) & 7 == 6
 
 
-def test_tree_pow2_root_cell_boxes():
-    """Under the power-of-two root every cell of level d is the cube of side
-    side / 2^d at the integer corner its key spells out (x, y, z bits of each
-    octant digit), and holds exactly its members: each member lies in it."""
+@pytest.mark.parametrize("root_mode", ["pow2", "tight"])
+def test_tree_cell_boxes(root_mode):
+    """Every cell of level d is the cube of side side / 2^d at the integer
+    corner its key spells out (x, y, z bits of each octant digit), and each
+    of its members lies in it -- under the power-of-two root and the tight
+    one alike."""
     pos, _ = clustered_halos(6000, 9, n_halo=40)
-    t = oracle.build_tree(pos, 8, root_mode="pow2")
+    t = oracle.build_tree(pos, 8, root_mode=root_mode)
     _check_invariants(t)
-    assert math.log2(t.side) == int(math.log2(t.side))
+    if root_mode == "pow2":
+        assert math.log2(t.side) == int(math.log2(t.side))
     p = pos.astype(np.float64)[t.perm]
     for c in range(t.n_cells):
         d = int(t.level[c])
